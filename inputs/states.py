@@ -1,0 +1,81 @@
+"""Seeded synthetic initial data, evaluated pointwise at given positions.
+
+Each function maps positions ``x`` [n, 3] to conserved variables
+``(rho, rho*u, rho*v, rho*w, rho*E)`` [n, 5] through the ideal-gas relation
+``rho*E = p/(gamma-1) + rho*|v|^2/2`` (Sec. 2).  These are the problem
+definitions of the workloads; they hold none of the scheme's arithmetic.
+Both the oracle and the CUDA path are initialised from the same values:
+nodal interpolation at the cell nodes.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def primitive_to_conserved(rho, vel, p, gamma=GAMMA):
+    rho = np.asarray(rho, np.float64)
+    vel = np.asarray(vel, np.float64)
+    p = np.asarray(p, np.float64)
+    out = np.empty(rho.shape + (5,), np.float64)
+    out[..., 0] = rho
+    out[..., 1:4] = rho[..., None] * vel
+    out[..., 4] = p / (gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=-1)
+    return out
+
+
+def conserved_to_primitive(q, gamma=GAMMA):
+    rho = q[..., 0]
+    vel = q[..., 1:4] / rho[..., None]
+    p = (gamma - 1.0) * (q[..., 4] - 0.5 * rho * np.sum(vel * vel, axis=-1))
+    return rho, vel, p
+
+
+def constant(x, rho=1.0, vel=(0.3, -0.2, 0.1), p=1.0, gamma=GAMMA):
+    n = len(x)
+    return primitive_to_conserved(np.full(n, rho), np.tile(np.asarray(vel, np.float64), (n, 1)),
+                                  np.full(n, p), gamma)
+
+
+def density_wave(x, t=0.0, amp=0.2, vel=(1.0, 1.0, 1.0), p=1.0, gamma=GAMMA):
+    """rho = 1 + amp*sin(2*pi*(x+y+z - (u+v+w) t)), uniform velocity and pressure."""
+    vel = np.asarray(vel, np.float64)
+    xs = np.asarray(x, np.float64) - vel * t
+    rho = 1.0 + amp * np.sin(2.0 * math.pi * xs.sum(axis=1))
+    n = len(rho)
+    return primitive_to_conserved(rho, np.tile(vel, (n, 1)), np.full(n, p), gamma)
+
+
+def spherical_riemann(x, centre=(0.0, 0.0, 0.0), radius=0.5, rho_in=1.0, rho_out=0.125,
+                      p_in=1.0, p_out=0.1, alpha0=None, gamma=GAMMA):
+    """Spherical explosion data (Sec. 5.4); with ``alpha0`` the erf-smoothed form.
+
+    The smoothed form is P = (P_out+P_in)/2 + (P_out-P_in)/2 * erf((r-R)/alpha0),
+    which tends to P_in inside and P_out outside.
+    """
+    from scipy.special import erf
+
+    r = np.linalg.norm(np.asarray(x, np.float64) - np.asarray(centre, np.float64), axis=1)
+    if alpha0 is None:
+        inside = r < radius
+        rho = np.where(inside, rho_in, rho_out)
+        p = np.where(inside, p_in, p_out)
+    else:
+        s = erf((r - radius) / alpha0)
+        rho = 0.5 * (rho_out + rho_in) + 0.5 * (rho_out - rho_in) * s
+        p = 0.5 * (p_out + p_in) + 0.5 * (p_out - p_in) * s
+    return primitive_to_conserved(rho, np.zeros((len(r), 3)), p, gamma)
+
+
+def taylor_green_3d(x, p0=100.0, gamma=GAMMA):
+    """u = sin x cos y cos z, v = -cos x sin y cos z, w = 0, rho = 1,
+    p = p0 + (cos 2x + cos 2y)(cos 2z + 2)/16."""
+    X, Y, Z = np.asarray(x, np.float64).T
+    u = np.sin(X) * np.cos(Y) * np.cos(Z)
+    v = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    w = np.zeros_like(u)
+    p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+    return primitive_to_conserved(np.ones_like(u), np.stack([u, v, w], 1), p, gamma)

@@ -1,0 +1,367 @@
+"""Pins of the oracle's mesh precompute and scheme against what the paper and the mathematics fix.
+
+* M_i, the quadrature-free volume and face integrals: reproduction of polynomials of
+  degree <= N (whose nodal interpolant is exact) against brute-force quadrature on the
+  raw sub-tet geometry.
+* The predictor's fixed point against a direct dense solve of the space-time system
+  built from the paper's definitions of K_1,i, F_0 and K_xi/eta/zeta by brute-force
+  space-time quadrature (linear advection, to which the density wave reduces exactly).
+* Whole step: free-stream preservation, discrete conservation, preservation of uniform
+  velocity and pressure, the CFL formula on a constant state, order N+1.
+* Limiter and viscous flux: closed forms and invariants.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import states
+from inputs.voronoi import box_voronoi, periodic_voronoi
+from oracle import scheme
+from oracle.mesh import from_polymesh
+
+_cache = {}
+
+
+def mesh(kind, n, N):
+    key = (kind, n, N)
+    if key not in _cache:
+        pm = periodic_voronoi(n) if kind == "per" else box_voronoi(n)
+        _cache[key] = (pm, from_polymesh(pm, N))
+    return _cache[key]
+
+
+def _poly(x, coeffs):
+    """A fixed polynomial of total degree <= 2 in x [n,3]; coeffs [10]."""
+    X, Y, Z = x.T
+    basis = np.stack([np.ones_like(X), X, Y, Z, X * X, Y * Y, Z * Z, X * Y, Y * Z, X * Z], 1)
+    return basis @ coeffs
+
+
+def _poly_grad(x, coeffs):
+    X, Y, Z = x.T
+    c = coeffs
+    gx = c[1] + 2 * c[4] * X + c[7] * Y + c[9] * Z
+    gy = c[2] + 2 * c[5] * Y + c[7] * X + c[8] * Z
+    gz = c[3] + 2 * c[6] * Z + c[8] * Y + c[9] * X
+    return np.stack([gx, gy, gz], 1)
+
+
+def _coeffs(rng, N):
+    c = rng.normal(size=10)
+    if N < 2:
+        c[4:] = 0.0
+    return c
+
+
+def _cell_quadrature(pm, i, n=6):
+    """Quadrature points/weights over cell i from the raw input sub-tets (no oracle topology)."""
+    xi, wq = scheme.tet_rule(n)
+    X = pm.subtet_coords()[pm.cell_subtet_ptr[i]:pm.cell_subtet_ptr[i + 1]]
+    pts, wts = [], []
+    for T in X:
+        J = np.stack([T[1] - T[0], T[2] - T[0], T[3] - T[0]], axis=1)
+        pts.append(T[0] + xi @ J.T)
+        wts.append(abs(np.linalg.det(J)) * wq)
+    return np.concatenate(pts), np.concatenate(wts)
+
+
+# ---------------------------------------------------------------------------
+# mesh precompute
+
+
+@pytest.mark.parametrize("kind,n", [("per", 2), ("box", 2)])
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_mass_matrix_invariants(kind, n, N):
+    pm, m = mesh(kind, n, N)
+    tot = 0.0
+    for cd in m.cells:
+        one = np.ones(len(cd.nodes))
+        assert abs(one @ cd.M @ one - cd.vol) < 1e-14 * max(1.0, cd.vol)   # partition of unity
+        assert np.all(np.linalg.eigvalsh(cd.M) > 0)
+        np.testing.assert_allclose(cd.M @ cd.Minv, np.eye(len(one)), atol=1e-9)
+        tot += cd.vol
+        # the cell boundary is closed: sum of area * outward normal = 0
+        s = sum(bt.area * bt.normal for bt in cd.bfaces)
+        assert np.linalg.norm(s) < 1e-13
+        assert abs(cd.h - 6 * cd.vol / sum(bt.area for bt in cd.bfaces)) < 1e-14
+    dom = np.prod(pm.hi - pm.lo)
+    if pm.periodic:
+        assert abs(tot - dom) < 1e-12
+    for cd in m.cells:
+        for bt in cd.bfaces:
+            if bt.nbr >= 0:
+                nb = m.cells[bt.nbr].bfaces[bt.nbr_tri]
+                assert abs(nb.area - bt.area) < 1e-14
+                np.testing.assert_allclose(nb.normal, -bt.normal, atol=1e-12)
+                np.testing.assert_allclose(m.cells[bt.nbr].nodes[nb.nodes] -
+                                           cd.nodes[bt.nodes], np.tile(
+                                               m.cells[bt.nbr].nodes[nb.nodes][0] - cd.nodes[bt.nodes][0],
+                                               (len(bt.nodes), 1)), atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_mass_matrix_reproduces_polynomial_integrals(N):
+    pm, m = mesh("per", 2, N)
+    rng = np.random.default_rng(1)
+    for i in range(m.n_cells):
+        cd = m.cells[i]
+        f, g = _coeffs(rng, N), _coeffs(rng, N)
+        xq, wq = _cell_quadrature(pm, i)
+        exact = np.sum(wq * _poly(xq, f) * _poly(xq, g))
+        fn, gn = _poly(cd.nodes, f), _poly(cd.nodes, g)
+        assert abs(fn @ cd.M @ gn - exact) < 1e-13 * max(1.0, abs(exact))
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_volume_term_reproduces_polynomial_integrals(N):
+    """sum_m vol[m] g(x_m) = int_{P_i} grad g . F for polynomial g, F of degree <= N."""
+    pm, m = mesh("per", 2, N)
+    R = m.R
+    rng = np.random.default_rng(2)
+    for i in range(m.n_cells):
+        cd = m.cells[i]
+        cF = [_coeffs(rng, N) for _ in range(3)]
+        g = _coeffs(rng, N)
+        # F at every sub-tet node, all 5 variables the same field
+        Fbar = np.zeros((len(cd.A), R.Np, 3, 5))
+        for k in range(len(cd.A)):
+            X = cd.X[k]
+            J = np.stack([X[1] - X[0], X[2] - X[0], X[3] - X[0]], axis=1)
+            xn = X[0] + R.nodes @ J.T
+            for e in range(3):
+                Fbar[k, :, e, :] = _poly(xn, cF[e])[:, None]
+        vol = scheme.volume_term(m, i, Fbar)
+        lhs = _poly(cd.nodes, g) @ vol[:, 2]
+        xq, wq = _cell_quadrature(pm, i)
+        gg = _poly_grad(xq, g)
+        Fq = np.stack([_poly(xq, cF[e]) for e in range(3)], 1)
+        exact = np.sum(wq * np.sum(gg * Fq, axis=1))
+        assert abs(lhs - exact) < 1e-12 * max(1.0, abs(exact))
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_face_term_reproduces_polynomial_integrals(N):
+    """sum_m face[m] g(x_m) = int_{dP_i} g G dS for polynomial g, G of degree <= N."""
+    pm, m = mesh("box", 2, N)
+    rng = np.random.default_rng(3)
+    x2, w2 = np.polynomial.legendre.leggauss(8)
+    x2, w2 = 0.5 * (x2 + 1), 0.5 * w2
+    a, b = np.meshgrid(x2, x2, indexing="ij")
+    wa, wb = np.meshgrid(w2, w2, indexing="ij")
+    uv = np.stack([a, b * (1 - a)], -1).reshape(-1, 2)
+    wt = (wa * wb * (1 - a)).ravel()                      # sums to 1/2
+    for i in range(m.n_cells):
+        cd = m.cells[i]
+        cG, g = _coeffs(rng, N), _coeffs(rng, N)
+        Gs = [np.repeat(_poly(cd.nodes[bt.nodes], cG)[:, None], 5, 1) for bt in cd.bfaces]
+        face = scheme.face_term(m, i, Gs)
+        lhs = _poly(cd.nodes, g) @ face[:, 0]
+        exact = 0.0
+        for bt in cd.bfaces:
+            P = cd.nodes[bt.nodes[[0, m.N, -1]]]    # the triangle's corners in lattice order
+            xq = P[0] + uv[:, :1] * (P[1] - P[0]) + uv[:, 1:] * (P[2] - P[0])
+            exact += 2 * bt.area * np.sum(wt * _poly(xq, g) * _poly(xq, cG))
+        assert abs(lhs - exact) < 1e-12 * max(1.0, abs(exact))
+
+
+# ---------------------------------------------------------------------------
+# predictor
+
+
+def test_predictor_constant_state_is_exact():
+    pm, m = mesh("per", 2, 2)
+    prm = scheme.Params()
+    u = states.constant(m.node_coords())
+    for i, ui in enumerate(m.split(u)):
+        q, it = scheme.predictor(m, i, ui, 0.01, 0.0, 0.0, prm)
+        assert it == 1 or it == 2
+        np.testing.assert_allclose(q, np.repeat(ui[:, None], m.R.Nt, 1), atol=1e-13)
+
+
+def _spacetime_direct(m, i, uhat, dt, a):
+    """Dense space-time system of Eq. ADER-localCauchy for linear advection q_t + a.grad q = 0,
+    with K_1,i, F_0 and K_d assembled from their defining integrals by quadrature."""
+    R = m.R
+    cd = m.cells[i]
+    Ni, Nt, Np = len(cd.nodes), R.Nt, R.Np
+    xi, wq = scheme.tet_rule(m.N + 3)
+    tg, tw = np.polynomial.legendre.leggauss(m.N + 3)
+    tg, tw = 0.5 * (tg + 1), 0.5 * tw
+    phi = R.eval_phi(xi)
+    dphi = R.eval_dphi(xi)
+    psi = np.array([[R.psi(s, t) for t in tg] for s in range(Nt)])         # [s, q]
+    dpsi = np.array([[R.dpsi_at(s, t) for t in tg] for s in range(Nt)])
+    psi1 = np.array([R.psi(s, 1.0) for s in range(Nt)])
+    psi0 = np.array([R.psi(s, 0.0) for s in range(Nt)])
+    mass_x = np.einsum("q,qj,ql->jl", wq, phi, phi)
+    stiff_x = np.einsum("q,qj,qdl->djl", wq, phi, dphi)
+    mass_t = np.einsum("q,sq,tq->st", tw, psi, psi)
+    k1_t = np.outer(psi1, psi1) - np.einsum("q,sq,tq->st", tw, dpsi, psi)
+    K1 = np.zeros((Ni * Nt, Ni * Nt))
+    F0 = np.zeros((Ni * Nt, Ni))
+    Kx = np.zeros((Ni * Nt, Ni * Nt))
+    for k in range(len(cd.A)):
+        A = cd.A[k]
+        det = cd.det[k]
+        coef = dt * cd.Jinv[k] @ a                                          # f*_d = dt sum_e Jinv[d,e] a_e q
+        for j in range(Np):
+            for l in range(Np):
+                for s in range(Nt):
+                    row = A[j] * Nt + s
+                    F0[row, A[l]] += det * psi0[s] * mass_x[j, l]
+                    for t in range(Nt):
+                        col = A[l] * Nt + t
+                        K1[row, col] += det * mass_x[j, l] * k1_t[s, t]
+                        Kx[row, col] += det * mass_t[s, t] * np.dot(coef, stiff_x[:, j, l])
+    sol = np.linalg.solve(K1 + Kx, F0 @ uhat)
+    return sol.reshape(Ni, Nt)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_predictor_fixed_point_equals_direct_spacetime_solve(N):
+    pm, m = mesh("per", 2, N)
+    prm = scheme.Params()
+    u = states.density_wave(m.node_coords())
+    dt = 0.004
+    for i in (0, 3):
+        ui = m.split(u)[i]
+        q, it = scheme.predictor(m, i, ui, dt, 0.0, 0.0, prm)
+        assert it < prm.picard_max
+        ref = _spacetime_direct(m, i, ui[:, 0], dt, np.array([1.0, 1.0, 1.0]))
+        np.testing.assert_allclose(q[:, :, 0], ref, rtol=0, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# whole step
+
+
+@pytest.mark.parametrize("kind", ["per", "box"])
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_free_stream_preservation(kind, N):
+    pm, m = mesh(kind, 2, N)
+    prm = scheme.Params()
+    uc = m.split(states.constant(m.node_coords()))
+    new, info = scheme.step(m, uc, prm)
+    err = max(np.abs(a - b).max() for a, b in zip(new, uc))
+    assert err < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_conservation_and_uniform_velocity_pressure(N):
+    pm, m = mesh("per", 2, N)
+    prm = scheme.Params()
+    uc = m.split(states.density_wave(m.node_coords()))
+    t0 = scheme.conserved_totals(m, uc)
+    new, info = scheme.step(m, uc, prm)
+    new, info = scheme.step(m, new, prm)
+    t1 = scheme.conserved_totals(m, new)
+    np.testing.assert_allclose(t1, t0, rtol=0, atol=1e-13 * np.abs(t0).max())
+    rho, v, p = scheme.primitives(np.concatenate(new), prm.gamma)
+    assert np.abs(v - 1).max() < 1e-12 and np.abs(p - 1).max() < 1e-12
+    assert info.iterations.max() < prm.picard_max
+
+
+def test_cfl_time_step_closed_form():
+    pm, m = mesh("per", 2, 2)
+    prm = scheme.Params(cfl=0.3)
+    u = states.constant(m.node_coords(), rho=1.2, vel=(0.3, -0.4, 0.0), p=0.8)
+    dt = scheme.cfl_dt(m, m.split(u), np.zeros(m.n_cells), prm)
+    lam = 0.5 + math.sqrt(1.4 * 0.8 / 1.2)
+    assert abs(dt - 0.3 * m.h_min / (5 * lam)) < 1e-15
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("N,ns,T", [(1, (3, 6), 0.03), (2, (2, 4), 0.02)])
+def test_order_of_accuracy_density_wave(N, ns, T):
+    """Observed L2 order of rho on the smooth density wave is about N+1 (Sec. 5.1-5.2)."""
+    errs, hs = [], []
+    for n in ns:
+        pm = periodic_voronoi(n)
+        m = from_polymesh(pm, N)
+        prm = scheme.Params(cfl=0.3)
+        uc = m.split(states.density_wave(m.node_coords()))
+        t = 0.0
+        dt0 = scheme.cfl_dt(m, uc, np.zeros(m.n_cells), prm)
+        nst = int(math.ceil(T / dt0))
+        for _ in range(nst):
+            uc, _ = scheme.step(m, uc, prm, dt=T / nst)
+        _, e2 = scheme.error_norms(m, uc, lambda x: states.density_wave(x, t=T))
+        errs.append(e2)
+        hs.append(1.0 / n)
+    order = math.log(errs[0] / errs[1]) / math.log(hs[0] / hs[1])
+    assert order > N + 0.5, (errs, order)
+
+
+# ---------------------------------------------------------------------------
+# limiter and viscous terms
+
+
+def test_limiter_quiet_on_smooth_data_and_active_under_compression():
+    pm, m = mesh("box", 3, 1)
+    prm = scheme.Params(limiter=True)
+    x = m.node_coords()
+    beta, mu = scheme.limiter(m, m.split(states.density_wave(x)), prm)
+    assert np.all(beta == 0) and np.all(mu == 0)
+    # strong compression toward the centre: v = -5 x
+    rho = np.ones(len(x))
+    u = states.primitive_to_conserved(rho, -5.0 * x, np.ones(len(x)))
+    beta, mu = scheme.limiter(m, m.split(u), prm)
+    assert np.all((beta >= 0) & (beta <= 1))
+    assert beta.max() == 1.0
+    interior = [i for i, c in enumerate(m.cells) if all(bt.nbr >= 0 for bt in c.bfaces)]
+    assert np.all(beta[interior] == 1.0)
+    assert np.all(mu[beta > 0] > 0)
+    # expansion never triggers
+    u = states.primitive_to_conserved(rho, 5.0 * x, np.ones(len(x)))
+    beta, _ = scheme.limiter(m, m.split(u), prm)
+    assert np.all(beta == 0)
+
+
+def test_limiter_off_on_smooth_data_leaves_step_unchanged():
+    pm, m = mesh("per", 2, 1)
+    uc = m.split(states.density_wave(m.node_coords()))
+    a, _ = scheme.step(m, uc, scheme.Params(limiter=False), dt=0.003)
+    b, _ = scheme.step(m, uc, scheme.Params(limiter=True), dt=0.003)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_viscous_flux_closed_forms():
+    prm = scheme.Params(gamma=1.4, R=1.0)
+    mu, kappa = 0.3, 0.7
+    # shear u = a y: sigma = p I - mu (grad v + grad v^T): sigma_xy = -mu a
+    a = 2.0
+    rho, p, y = 1.3, 0.9, 0.25
+    Q = states.primitive_to_conserved(np.array([rho]), np.array([[a * y, 0, 0]]), np.array([p]))
+    grad = np.zeros((1, 3, 5))
+    grad[0, 1, 1] = rho * a                     # d(rho u)/dy
+    grad[0, 1, 4] = rho * (a * y) * a           # d(rho E)/dy with p, rho uniform
+    F = scheme.flux(Q, grad, mu, 0.0, prm)[0]
+    assert abs(F[1, 1] - (0.0 - mu * a)) < 1e-14              # y-flux of x-momentum
+    assert abs(F[0, 2] - (0.0 - mu * a)) < 1e-14              # x-flux of y-momentum
+    assert abs(F[1, 4] - (a * y) * (-mu * a)) < 1e-14          # energy: v . sigma
+    # heat: T = p/(rho R) with p linear in x -> dT/dx = (dp/dx)/(rho R)
+    Q = states.primitive_to_conserved(np.array([rho]), np.zeros((1, 3)), np.array([p]))
+    grad = np.zeros((1, 3, 5))
+    grad[0, 0, 4] = 0.5 / (prm.gamma - 1)       # dp/dx = 0.5
+    F = scheme.flux(Q, grad, 0.0, kappa, prm)[0]
+    assert abs(F[0, 4] - (-kappa * 0.5 / (rho * prm.R))) < 1e-14
+    # viscous eigenvalues: max(4 mu/(3 rho), kappa/(c_v rho))
+    assert abs(scheme.viscous_eigen(2.0, 0.3, 0.0, prm) - 0.2) < 1e-15
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_navier_stokes_step_free_stream_and_conservation(N):
+    pm, m = mesh("per", 2, N)
+    # mu small enough for the fixed-point iteration to contract on the fan subgrid
+    prm = scheme.Params(mu=0.005, kappa=-1.0, Pr=0.71)
+    uc = m.split(states.constant(m.node_coords()))
+    new, _ = scheme.step(m, uc, prm)
+    assert max(np.abs(a - b).max() for a, b in zip(new, uc)) < 1e-12
+    uc = m.split(states.taylor_green_3d(2 * math.pi * m.node_coords(), p0=10.0))
+    t0 = scheme.conserved_totals(m, uc)
+    new, info = scheme.step(m, uc, prm)
+    t1 = scheme.conserved_totals(m, new)
+    np.testing.assert_allclose(t1, t0, rtol=0, atol=1e-12 * np.abs(t0).max())
+    assert info.iterations.max() < prm.picard_max
