@@ -1,0 +1,192 @@
+/*
+ * afe.h - C ABI of the GB300 (sm_103a) quadrature-free ADER-AFE-DG step on 3D polyhedral meshes.
+ *
+ * The operation is one explicit ADER step of the agglomerated-finite-element (AFE)
+ * discontinuous Galerkin scheme of arXiv 2605.00619 over every polyhedral cell:
+ *   - artificial-viscosity detector (Sec. 4.5, Eqs. divergence3D and beta3D),
+ *   - CFL time step (Sec. 4.2, Eq. timestep),
+ *   - element-local space-time Galerkin predictor, a fixed-point iteration on the
+ *     cell's continuous nodal subgrid DOFs (Sec. 4.3, Eqs. ADER-localCauchy, ader4),
+ *   - time-integrated predictor and fluxes (Eq. TAvectors),
+ *   - Rusanov fluxes on the sub-triangles of each polygonal face (Sec. 4.4, Eq. 3.33),
+ *   - corrector update M_i (u^{n+1} - u^n) = volume term - face term (Sec. 4.4).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an afe_status; outputs go through out-parameters.
+ *   - On error a message is available from afe_last_error() (thread-local), and the
+ *     mesh handle keeps its last valid state.
+ *   - The library copies every input array; the caller owns all host buffers and the
+ *     handle owns all device memory it allocates.  Device pointers passed in
+ *     (afe_set_state_device, afe_get_state_device) stay owned by the caller.
+ *   - Conserved variables are ordered (rho, rho*u, rho*v, rho*w, rho*E); states are
+ *     node-major [n_nodes][5] FP64.  The node order is the library's own: contiguous per
+ *     cell (cell i owns nodes node_ptr[i] .. node_ptr[i+1]-1); afe_get_node_coords gives
+ *     their positions, so initial data is set by nodal interpolation there.
+ *   - All GPU work of a handle runs on its stream (afe_mesh_create's cuda_stream, or
+ *     afe_set_stream); entry points that return host data synchronise that stream.
+ *   - There is no CPU fallback: without a usable CUDA device every call that needs the
+ *     GPU returns AFE_ECUDA.
+ */
+#ifndef AFE_H
+#define AFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AFE_OK = 0,
+  AFE_EINVAL = 1,     /* bad argument (null pointer, size, unsupported option)           */
+  AFE_EMESH = 2,      /* invalid mesh: degenerate sub-tet, non-conforming subgrid, a cell
+                         whose subgrid is not a ball, an unmatched face on a periodic mesh */
+  AFE_ENOMEM = 3,     /* device or host allocation failed                                  */
+  AFE_ECUDA = 4,      /* CUDA runtime error (message names the call)                       */
+  AFE_ENOCONV = 5,    /* the predictor hit picard_max in at least one cell (step applied)   */
+  AFE_ENONFINITE = 6, /* NaN/Inf or non-positive density or pressure after the step        */
+  AFE_ETIMEOUT = 7    /* a bounded wait on device progress gave up                          */
+} afe_status;
+
+typedef enum { AFE_EULER = 0, AFE_NAVIER_STOKES = 1 } afe_equations;
+/* AFE_FP64: every step of the path in FP64.  AFE_FP32: predictor, face fluxes and the
+ * corrector's inverse-mass apply in FP32, with FP64 master state, FP64 CFL reduction and
+ * an FP64 correction of each cell's conserved totals. */
+typedef enum { AFE_FP64 = 0, AFE_FP32 = 1 } afe_precision;
+typedef enum { AFE_BC_PERIODIC = 0, AFE_BC_TRANSMISSIVE = 1 } afe_bc;
+
+typedef struct {
+  int order;          /* polynomial degree N in {1, 2, 3} (Sec. 4.1)                           */
+  int equations;      /* afe_equations; Euler ignores mu, Pr, kappa unless the limiter adds mu */
+  int precision;      /* afe_precision                                                         */
+  double gamma;       /* ratio of specific heats (Sec. 2)                                      */
+  double R;           /* gas constant; c_v = R / (gamma - 1)                                  */
+  double mu;          /* dynamic viscosity (Navier-Stokes)                                     */
+  double Pr;          /* Prandtl number, used when kappa < 0                                   */
+  double kappa;       /* heat conduction; < 0 selects kappa_i = mu_i * gamma * c_v / Pr        */
+  double cfl;         /* CFL number of Eq. timestep                                            */
+  int limiter;        /* 1: artificial-viscosity limiter of Sec. 4.5                            */
+  double m1;          /* detector constant m_1 of Eq. beta3D (0.1 in the paper)                */
+  double picard_tol;  /* stop when max|q^{r+1}-q^r| <= tol * max(1, max|q^r|), per cell       */
+  int picard_max;     /* iteration cap; hitting it is reported as AFE_ENOCONV                  */
+  double period[3];   /* domain period per axis; used for sub-tet vertices with image shifts   */
+} afe_params;
+
+typedef struct {
+  double dt;            /* last time step                                        */
+  double t;             /* accumulated simulation time                           */
+  int64_t steps;        /* completed steps                                       */
+  double picard_mean;   /* mean predictor iterations over cells, last step       */
+  int32_t picard_max;   /* max predictor iterations over cells, last step        */
+  int64_t nonconverged; /* cells that hit picard_max, last step                  */
+  int64_t troubled;     /* cells with beta_i > 0, last step                      */
+  double totals[5];     /* sum_i 1^T M_i u_i per conserved variable (FP64)       */
+} afe_stats;
+
+typedef struct afe_mesh afe_mesh; /* opaque; owns all device memory of one simulation */
+
+/* Fill *p with the paper's settings (Sec. 5: gamma 1.4, R 1, kappa 0, CFL 0.3, m_1 0.1,
+ * tolerance 1e-12) for degree `order`, FP64, Euler, no limiter, picard_max 64. */
+afe_status afe_default_params(afe_params* p, int order);
+
+/* Build a mesh from polyhedra and their tetrahedral subgrid (Sec. 4.1) and run the FP64
+ * set-up on the GPU: sub-tet Jacobians, cell mass matrices M_i (Sec. 4.4), their inverses
+ * (stored per cell, Sec. 4.3), face matching, characteristic lengths.
+ *   xyz             [n_vertices][3] vertex positions (host).
+ *   cell_subtet_ptr [n_cells + 1] CSR offsets into the sub-tets (host); n_subtets = ptr[n_cells].
+ *   subtet_vtx      [n_subtets][4] global vertex ids (host).
+ *   subtet_shift    [n_subtets][4][3] periodic image of each sub-tet vertex, or NULL; a vertex
+ *                   sits at xyz[id] + shift * period (host).
+ *   boundary        afe_bc: periodic (every cell-boundary triangle must be matched) or
+ *                   transmissive (unmatched triangles are domain boundary, outer state = inner).
+ *   cuda_stream     cudaStream_t for all work of the handle (NULL = legacy default stream).
+ * Sub-tets with negative orientation are reoriented; a zero-volume sub-tet, a non-conforming
+ * subgrid or a cell that is not a topological ball returns AFE_EMESH. */
+afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double* xyz,
+                           int64_t n_cells, const int64_t* cell_subtet_ptr,
+                           const int64_t* subtet_vtx, const int8_t* subtet_shift, int boundary,
+                           void* cuda_stream, afe_mesh** out);
+
+/* Host-only validation of the same inputs as afe_mesh_create (no GPU is touched): builds the
+ * topology and returns AFE_OK, AFE_EINVAL or AFE_EMESH, with the number of AFE nodes and of
+ * cell-boundary sub-triangles in *n_nodes / *n_face_tris (either may be NULL). */
+afe_status afe_mesh_validate(const afe_params* p, int64_t n_vertices, const double* xyz,
+                             int64_t n_cells, const int64_t* cell_subtet_ptr,
+                             const int64_t* subtet_vtx, const int8_t* subtet_shift, int boundary,
+                             int64_t* n_nodes, int64_t* n_face_tris);
+
+/* Number of AFE nodes (DOF points) and, if node_ptr is not NULL, the per-cell offsets
+ * [n_cells + 1] (host). */
+afe_status afe_num_nodes(const afe_mesh* m, int64_t* n_nodes, int64_t* node_ptr);
+
+/* Node positions [n_nodes][3] (host); nodes of cells touching a periodic boundary are given
+ * in the frame of their own cell. */
+afe_status afe_get_node_coords(const afe_mesh* m, double* xyz);
+
+/* Replace the stream used by the handle. */
+afe_status afe_set_stream(afe_mesh* m, void* cuda_stream);
+
+/* Set the conserved state u^n from a host array [n_nodes][5] FP64 (synchronous copy). */
+afe_status afe_set_state(afe_mesh* m, const double* q);
+
+/* Set the state from a device array [n_nodes][5] FP64, ordered on `cuda_stream`
+ * (NULL = the handle's stream); the copy is device-to-device and asynchronous. */
+afe_status afe_set_state_device(afe_mesh* m, const double* dq, void* cuda_stream);
+
+/* Copy the state to a host array [n_nodes][5] FP64 (synchronises the handle's stream). */
+afe_status afe_get_state(const afe_mesh* m, double* q);
+
+/* Copy the state to a device array [n_nodes][5] FP64 on the handle's stream (asynchronous). */
+afe_status afe_get_state_device(const afe_mesh* m, double* dq);
+
+/* CFL time step of Eq. timestep at the current state (FP64 reduction on the GPU; includes
+ * the limiter's artificial viscosity when the limiter is on). */
+afe_status afe_compute_dt(afe_mesh* m, double* dt);
+
+/* One ADER-AFE-DG step.  dt > 0: use it; dt <= 0: the CFL time step, computed and kept on
+ * the device.  Waits for the step and returns AFE_ENOCONV / AFE_ENONFINITE if a cell did
+ * not converge or the new state is not admissible (the step is applied either way). */
+afe_status afe_step(afe_mesh* m, double dt);
+
+/* `nsteps` steps enqueued back to back on the handle's stream with no host synchronisation
+ * between them (dt as in afe_step); returns after enqueueing.  Status flags accumulate and
+ * are reported by afe_get_stats / afe_sync. */
+afe_status afe_step_async(afe_mesh* m, double dt, int nsteps);
+
+/* Wait for the handle's stream and return the accumulated status of afe_step_async calls
+ * (AFE_OK, AFE_ENOCONV or AFE_ENONFINITE), clearing it. */
+afe_status afe_sync(afe_mesh* m);
+
+/* Statistics of the last step plus FP64 conserved totals of the current state. */
+afe_status afe_get_stats(const afe_mesh* m, afe_stats* s);
+
+/* Diagnostics of the last step (host arrays, NULL to skip): the time-integrated predictor
+ * q_bar at every node [n_nodes][5] (Eq. TAvectors; recorded only after
+ * afe_set_diagnostics(m, 1)), predictor iterations per cell [n_cells], beta_i and mu_i per
+ * cell [n_cells]. */
+afe_status afe_set_diagnostics(afe_mesh* m, int on);
+afe_status afe_get_diagnostics(const afe_mesh* m, double* qbar, int32_t* iterations,
+                               double* beta, double* mu);
+
+/* Per-stage device timing.  With profiling on, every step records CUDA events on the
+ * handle's stream around its stages; afe_stage_times adds up the elapsed milliseconds of all
+ * steps since the last reset into ms[4] = {limiter + time step, predictor, face fluxes,
+ * corrector} and the number of steps into *nsteps, synchronising the stream (reset != 0
+ * clears the record). */
+afe_status afe_set_profiling(afe_mesh* m, int on);
+afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset);
+
+/* Bytes of device memory held by the handle. */
+afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* afe_last_error(void);
+
+/* Release the handle and all its device memory (NULL is ignored). */
+void afe_mesh_destroy(afe_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFE_H */

@@ -17,9 +17,19 @@ Recipe
 * Box ``[lo, hi]^3`` (transmissive boundaries): the Voronoi tessellation of the
   seeds and their mirror images across the six box planes, so that every cell
   is the Voronoi cell clipped to the box.
+* Quality step: Voronoi edges shorter than ``COLLAPSE`` times the lattice spacing
+  are collapsed (their end points merged topologically).  Short edges give
+  needle-shaped fan sub-tets whose tiny support makes the element-local
+  operators stiff enough to stall the predictor's fixed-point iteration; this
+  step stands in for the admissible-cell guarantee of the paper's own mesh
+  generator (Sec. 3).  A merge that would fold a sub-tet is skipped.
+* Lloyd step: before the tessellation used, each jittered seed is moved once to
+  the volume centroid of its own Voronoi cell.  Together with the collapse this
+  removes the thin faces and needle sub-tets that otherwise leave a few cells per
+  thousand with a divergent predictor iteration at CFL 0.3.
 * Fan subgrid: each cell is split by joining its centre (the mean of its
-  Voronoi vertices) to a fan triangulation of each face about the face centre
-  (the mean of the face's vertices): one sub-tet per face edge.
+  vertices) to a fan triangulation of each face about the face centre (the mean
+  of the face's vertices): one sub-tet per face edge.
 
 Array form (matches ``afe_mesh_create``)
 ----------------------------------------
@@ -38,6 +48,8 @@ from scipy.spatial import Voronoi
 JITTER = 0.3
 # Voronoi edges shorter than COLLAPSE * (lattice spacing) are collapsed
 COLLAPSE = 0.2
+# Lloyd steps applied to the jittered seeds (each moves a seed to its cell's centroid)
+LLOYD = 1
 
 
 @dataclass
@@ -77,121 +89,211 @@ def jittered_seeds(n: int, lo: float, hi: float, seed: int) -> np.ndarray:
     return (lo + (idx + 0.5 + jit) * (hi - lo) / n).reshape(-1, 3)
 
 
-def _order_polygon(pts: np.ndarray, normal: np.ndarray) -> np.ndarray:
-    """Indices ordering the vertices of a convex planar polygon counter-clockwise about ``normal``."""
-    c = pts.mean(axis=0)
-    nrm = normal / np.linalg.norm(normal)
-    a = pts[0] - c
-    a = a - nrm * (a @ nrm)
-    a /= np.linalg.norm(a)
-    b = np.cross(nrm, a)
-    d = pts - c
-    ang = np.arctan2(d @ b, d @ a)
-    return np.argsort(ang, kind="stable")
+class _Fold(Exception):
+    """A non-positive fan sub-tet: ``near`` holds the vertices of the offending edges,
+    ``face`` all vertices of the faces involved."""
+
+    def __init__(self, near, face=None):
+        super().__init__("folded fan sub-tet")
+        self.near = list(near)
+        self.face = list(face if face is not None else near)
 
 
-def _fan_subtets(cell_polys, cc_id, fc_ids, out_vtx, out_shift, fc_shifts, positions):
-    """Append the fan sub-tets of one cell.
+def _original_faces(vor, P, C):
+    """Faces of the original cells (< C) as flat arrays: cell, neighbour point, CSR offsets
+    and scipy vertex ids ordered counter-clockwise about the outward normal."""
+    rp = vor.ridge_points
+    sel = np.nonzero((rp[:, 0] < C) | (rp[:, 1] < C))[0]
+    cells, nbrs, rid = [], [], []
+    for a_is in (0, 1):
+        side = sel[rp[sel, a_is] < C]
+        cells.append(rp[side, a_is])
+        nbrs.append(rp[side, 1 - a_is])
+        rid.append(side)
+    cells = np.concatenate(cells)
+    nbrs = np.concatenate(nbrs)
+    rid = np.concatenate(rid)
+    order = np.lexsort((rid, cells))
+    cells, nbrs, rid = cells[order], nbrs[order], rid[order]
+    verts = [vor.ridge_vertices[r] for r in rid]
+    cnt = np.array([len(v) for v in verts])
+    ptr = np.concatenate([[0], np.cumsum(cnt)])
+    flat = np.concatenate([np.asarray(v) for v in verts])
+    if np.any(flat < 0):
+        raise RuntimeError("unbounded ridge next to an original cell; margin too small")
+    # qhull lists the vertices of a 3-d ridge in cyclic order; orient about the outward normal
+    X = vor.vertices[flat]
+    nxt = np.arange(len(flat)) + 1
+    nxt[ptr[1:] - 1] = ptr[:-1]
+    area = np.add.reduceat(np.cross(X, X[nxt]), ptr[:-1], axis=0)
+    flip = np.einsum("fd,fd->f", area, P[nbrs] - P[cells]) < 0
+    fidx = np.repeat(np.arange(len(cnt)), cnt)
+    local = np.arange(len(flat)) - ptr[fidx]
+    src = np.where(flip[fidx], ptr[fidx] + cnt[fidx] - 1 - local, np.arange(len(flat)))
+    return cells, nbrs, ptr, flat[src]
 
-    cell_polys: list of (vertex ids, vertex shifts) per face, ordered CCW seen from outside.
-    positions: callable (ids, shifts) -> coords in the cell frame.
+
+def _next_index(ptr):
+    nxt = np.arange(ptr[-1]) + 1
+    nxt[ptr[1:] - 1] = ptr[:-1]
+    return nxt
+
+
+def _collapse(pos, ptr, fv, fs, L, tol, exclude):
+    """Union-find merge of the end points of Voronoi edges shorter than tol.
+
+    pos: canonical vertex positions [nv, 3]; (ptr, fv, fs): per face the vertex ids and their
+    image shifts in the cell frame.  A vertex in ``exclude`` is never merged.  Returns merged
+    positions, the new faces (ptr, fv, fs), kept face indices, merge count and the members
+    of each merged vertex.
     """
-    cc_pos = positions(np.array([cc_id]), np.zeros((1, 3), np.int64))[0]
-    for f, (vids, vsh) in enumerate(cell_polys):
-        m = len(vids)
-        fc = fc_ids[f]
-        fsh = fc_shifts[f]
-        fpos = positions(np.array([fc]), fsh[None])[0]
-        vpos = positions(vids, vsh)
-        for e in range(m):
-            a, b = e, (e + 1) % m
-            J = np.stack([fpos - cc_pos, vpos[a] - cc_pos, vpos[b] - cc_pos], axis=1)
-            if not np.linalg.det(J) > 0:
-                raise RuntimeError("folded fan sub-tet (face polygon not star-shaped about its centre)")
-            out_vtx.append((cc_id, fc, vids[a], vids[b]))
-            out_shift.append((np.zeros(3, np.int64), fsh, vsh[a], vsh[b]))
-
-
-def _collapse_short_edges(vpos, cell_polys_all, L, tol):
-    """Merge the end points of every Voronoi edge shorter than ``tol``.
-
-    Short Voronoi edges give needle-shaped fan sub-tets, whose tiny support makes
-    the cell operators stiff; this plays the role of the quality step of the
-    paper's own mesh generator (Sec. 3: admissible control volumes).  Vertices
-    are merged topologically (union-find over canonical vertex ids, with the
-    periodic image offset of each merge), so every cell sees the same merge.
-    Faces left with fewer than three distinct vertices disappear on both sides.
-    Returns the new vertex positions and polygons, and the number of merges.
-    """
-    nv = len(vpos)
-    parent = list(range(nv))
-    off = [np.zeros(3, np.int64) for _ in range(nv)]
+    nv = len(pos)
+    parent = np.arange(nv)
+    off = np.zeros((nv, 3), np.int64)
     Lf = 0.0 if L is None else L
+    nxt = _next_index(ptr)
+    P = pos[fv] + fs * Lf
+    d = np.linalg.norm(P - P[nxt], axis=1)
 
     def find(x):
         o = np.zeros(3, np.int64)
-        path = []
         while parent[x] != x:
-            path.append(x)
             o = o + off[x]
             x = parent[x]
-        # path compression
-        acc = o.copy()
-        for y in path:
-            nxt = acc - off[y]
-            off[y] = acc
-            parent[y] = x
-            acc = nxt
         return x, o
 
     merges = 0
-    for polys in cell_polys_all:
-        for ids, shs, _ in polys:
-            m = len(ids)
-            for e in range(m):
-                a, b = int(ids[e]), int(ids[(e + 1) % m])
-                pa = vpos[a] + shs[e] * Lf
-                pb = vpos[b] + shs[(e + 1) % m] * Lf
-                if np.linalg.norm(pa - pb) >= tol:
-                    continue
-                ra, oa = find(a)
-                rb, ob = find(b)
-                rel = oa + shs[e] - ob - shs[(e + 1) % m]
-                if ra == rb:
-                    if np.any(rel != 0):
-                        raise RuntimeError("short-edge cluster wraps around the period")
-                    continue
-                parent[rb] = ra
-                off[rb] = rel
-                merges += 1
-    members: dict = {}
-    for x in range(nv):
-        r, o = find(x)
-        members.setdefault(r, []).append(vpos[x] - o * Lf)
-    new_id = {r: i for i, r in enumerate(members)}
-    new_pos = [np.mean(members[r], axis=0) for r in members]
-    out = []
-    for polys in cell_polys_all:
-        npolys = []
-        for ids, shs, b in polys:
-            vs = []
-            for i, sh in zip(ids, shs):
-                r, o = find(int(i))
-                vs.append((new_id[r], tuple(int(x) for x in sh + o)))
-            ded = [v for k, v in enumerate(vs) if v != vs[k - 1]] if len(set(vs)) > 1 else vs[:1]
-            if len(set(ded)) != len(ded):
-                raise RuntimeError("pinched face after edge collapse")
-            if len(ded) < 3:
-                continue
-            npolys.append((np.array([v[0] for v in ded], np.int64),
-                           np.array([v[1] for v in ded], np.int64), b))
-        out.append(npolys)
-    return new_pos, out, merges
+    for e in np.nonzero(d < tol)[0]:
+        a, b = int(fv[e]), int(fv[nxt[e]])
+        if a in exclude or b in exclude:
+            continue
+        ra, oa = find(a)
+        rb, ob = find(b)
+        rel = oa + fs[e] - ob - fs[nxt[e]]
+        if ra == rb:
+            if np.any(rel != 0):
+                raise RuntimeError("short-edge cluster wraps around the period")
+            continue
+        parent[rb] = ra
+        off[rb] = rel
+        merges += 1
+    # pointer jumping: root of every vertex and its image offset relative to the root
+    p = parent.copy()
+    roff = off.copy()
+    while True:
+        pp = p[p]
+        if np.array_equal(pp, p):
+            break
+        roff = roff + roff[p]
+        p = pp
+    uniq, new_id = np.unique(p, return_inverse=True)
+    size = np.bincount(new_id)
+    order = np.argsort(new_id, kind="stable")
+    bounds = np.concatenate([[0], np.cumsum(size)])
+    members = [order[bounds[i]:bounds[i + 1]].tolist() for i in range(len(uniq))]
+    acc = np.zeros((len(uniq), 3))
+    np.add.at(acc, new_id, pos - roff * Lf)
+    new_pos = acc / size[:, None]
+    ids = new_id[fv]
+    sh = fs + roff[fv]
+    # drop cyclically repeated vertices (collapsed edges), then faces left with < 3 vertices
+    same = (ids == ids[nxt]) & np.all(sh == sh[nxt], axis=1)
+    keep_e = ~same
+    cnt2 = np.add.reduceat(keep_e.astype(np.int64), ptr[:-1])
+    fidx = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr))
+    # a face whose vertices all merged keeps none; a pinched face repeats a vertex
+    rows = np.concatenate([fidx[keep_e][:, None], ids[keep_e][:, None], sh[keep_e]], 1)
+    nuniq = np.bincount(np.unique(rows, axis=0)[:, 0], minlength=len(ptr) - 1)
+    pinched = np.nonzero(nuniq != cnt2)[0]
+    if len(pinched):
+        f = int(pinched[0])
+        raise _Fold([int(x) for x in ids[ptr[f]:ptr[f + 1]]])
+    keep_f = cnt2 >= 3
+    keep_e &= keep_f[fidx]
+    cnt3 = cnt2[keep_f]
+    ptr2 = np.concatenate([[0], np.cumsum(cnt3)])
+    return new_pos, ptr2, ids[keep_e], sh[keep_e], np.nonzero(keep_f)[0], merges, members
 
 
-def periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE) -> PolyMesh:
+def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
+    """Face centres, cell centres and fan sub-tets; raises _Fold on a non-positive sub-tet."""
+    Lf = 0.0 if L is None else L
+    cnt = np.diff(ptr)
+    X = pos[fv] + fs * Lf
+    fpos = np.add.reduceat(X, ptr[:-1], axis=0) / cnt[:, None]
+    # face centres: one vertex per face pair, in a canonical frame
+    key_id: dict = {}
+    extra = []
+    nf = len(cnt)
+    fc_id = np.empty(nf, np.int64)
+    fc_sh = np.empty((nf, 3), np.int64)
+    for f in range(nf):
+        key, rs = face_key(f)
+        if key not in key_id:
+            key_id[key] = len(pos) + len(extra)
+            extra.append(fpos[f] - rs * Lf)
+        fc_id[f] = key_id[key]
+        fc_sh[f] = rs
+    fidx = np.repeat(np.arange(nf), cnt)
+    fcell = cells[fidx]
+    # cell centres: mean of the distinct vertices of each cell
+    rows = np.concatenate([fcell[:, None], fv[:, None], fs], 1)
+    u = np.unique(rows, axis=0)
+    upos = pos[u[:, 1]] + u[:, 2:] * Lf
+    csum = np.zeros((C, 3))
+    np.add.at(csum, u[:, 0], upos)
+    ccen = csum / np.bincount(u[:, 0], minlength=C)[:, None]
+    cc_id = len(pos) + len(extra) + np.arange(C)
+    xyz = np.concatenate([pos, np.asarray(extra).reshape(-1, 3), ccen])
+    # fan sub-tets (cell centre, face centre, v_i, v_i+1)
+    nxt = _next_index(ptr)
+    vtx = np.stack([cc_id[fcell], fc_id[fidx], fv, fv[nxt]], 1)
+    sh = np.stack([np.zeros_like(fs), fc_sh[fidx], fs, fs[nxt]], 1)
+    P = xyz[vtx] + sh * Lf
+    det = np.linalg.det(np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], -1))
+    bad = np.nonzero(~(det > 0))[0]
+    if len(bad):
+        near = sorted({int(v) for j in bad for v in (fv[j], fv[nxt[j]])})
+        face = sorted({int(v) for f in set(fidx[bad].tolist()) for v in fv[ptr[f]:ptr[f + 1]]})
+        raise _Fold(near, face)
+    sub_ptr = np.concatenate([[0], np.cumsum(np.bincount(fcell, minlength=C))])
+    return xyz, sub_ptr, vtx, sh
+
+
+def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of):
+    exclude: set = set()
+    for _ in range(200):
+        if tol > 0:
+            new_pos, ptr2, fv2, fs2, keep, merges, members = _collapse(pos, ptr, fv, fs, L, tol, exclude)
+        else:
+            new_pos, ptr2, fv2, fs2, keep, merges = pos, ptr, fv, fs, np.arange(len(ptr) - 1), 0
+            members = [[i] for i in range(len(pos))]
+        try:
+            kc = cells[keep]
+            kn = nbrs[keep]
+            xyz, sub_ptr, vtx, sh = _fan(new_pos, kc, ptr2, fv2, fs2, L, C, lambda f: face_key_of(kc[f], kn[f]))
+        except _Fold as e:
+            # undo the fewest merges: first those at the folded edges, then the whole face
+            for group in (e.near, e.face):
+                grow = set()
+                for v in group:
+                    if len(members[v]) > 1:
+                        grow |= set(members[v])
+                if not grow <= exclude:
+                    break
+            else:
+                raise RuntimeError("cannot build a fold-free fan subgrid")
+            exclude |= grow
+            continue
+        return xyz, sub_ptr, vtx, sh, merges, len(new_pos), np.bincount(kc, minlength=C)
+    raise RuntimeError("edge collapse did not settle")
+
+
+def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
+                      seeds: np.ndarray | None = None) -> PolyMesh:
     """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids."""
-    seeds = jittered_seeds(n, 0.0, L, seed)
+    if seeds is None:
+        seeds = jittered_seeds(n, 0.0, L, seed)
     C = n ** 3
     margin = min(2.5 * L / n, L)
     pts, pid, psh = [seeds], [np.arange(C)], [np.zeros((C, 3), np.int64)]
@@ -210,117 +312,58 @@ def periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = CO
     pid = np.concatenate(pid)
     psh = np.concatenate(psh)
     vor = Voronoi(P)
+    cells, nbrs, ptr, flat = _original_faces(vor, P, C)
 
     # generators of every Voronoi vertex (points whose region holds it)
-    gens: dict[int, list[int]] = {}
+    gens: dict = {}
     for p in range(len(P)):
         for v in vor.regions[vor.point_region[p]]:
             if v >= 0:
                 gens.setdefault(v, []).append(p)
 
     def canon(members):
-        """Canonical translate of a generator set: (key, shift of the frame)."""
-        lab = [(int(pid[p]), tuple(int(x) for x in psh[p])) for p in members]
-        ref = min(lab)
-        rs = np.array(ref[1])
-        key = tuple(sorted((s, tuple(int(x) for x in np.array(sh) - rs)) for s, sh in lab))
-        return key, rs
+        """Canonical translate of a set of generators: (key, image shift of the frame)."""
+        lab = sorted((int(pid[p]), tuple(int(x) for x in psh[p])) for p in members)
+        ref = lab[0]
+        key = tuple((s, (sh[0] - ref[1][0], sh[1] - ref[1][1], sh[2] - ref[1][2])) for s, sh in lab)
+        return key, np.array(ref[1])
 
-    vkey_id: dict = {}
+    used = np.unique(flat)
+    vkey: dict = {}
     vpos: list = []
-    vcache: dict[int, tuple[int, np.ndarray]] = {}
-
-    def vertex(v):
-        if v in vcache:
-            return vcache[v]
-        key, rs = canon(gens[v])
-        if key not in vkey_id:
-            vkey_id[key] = len(vpos)
+    vid = np.empty(len(used), np.int64)
+    vsh = np.empty((len(used), 3), np.int64)
+    for u, v in enumerate(used):
+        key, rs = canon(gens[int(v)])
+        if key not in vkey:
+            vkey[key] = len(vpos)
             vpos.append(vor.vertices[v] - rs * L)
-        out = (vkey_id[key], rs)
-        vcache[v] = out
-        return out
+        vid[u] = vkey[key]
+        vsh[u] = rs
+    loc = np.searchsorted(used, flat)
+    fv = vid[loc]
+    fs = vsh[loc]
+    pos = np.array(vpos)
 
-    # ridges of original cells
-    ridges_of = [[] for _ in range(C)]
-    for r, (a, b) in enumerate(vor.ridge_points):
-        if a < C:
-            ridges_of[a].append((r, b))
-        if b < C:
-            ridges_of[b].append((r, a))
+    def face_key_of(a, b):
+        return canon([a, b])
 
-    cell_polys_all = []
-    for a in range(C):
-        polys = []
-        for r, b in ridges_of[a]:
-            rv = vor.ridge_vertices[r]
-            if -1 in rv:
-                raise RuntimeError("unbounded ridge next to an original cell; margin too small")
-            rv = np.array(rv)
-            nrm = P[b] - P[a]
-            order = _order_polygon(vor.vertices[rv], nrm)
-            rv = rv[order]
-            ids, shs = zip(*(vertex(int(v)) for v in rv))
-            polys.append((np.array(ids, np.int64), np.array(shs, np.int64), b))
-        cell_polys_all.append(polys)
-    merges = 0
-    if collapse > 0:
-        vpos, cell_polys_all, merges = _collapse_short_edges(vpos, cell_polys_all, L, collapse * L / n)
-    n_voro = len(vpos)
-    xyz_list = list(vpos)
-
-    def positions(ids, shifts):
-        return np.array([xyz_list[i] for i in ids]) + np.asarray(shifts, np.float64) * L
-
-    # face centres (canonical per generator pair), then cell centres
-    fkey_id: dict = {}
-    sub_vtx, sub_sh, ptr, nfaces = [], [], [0], []
-    for a in range(C):
-        polys = cell_polys_all[a]
-        fc_ids, fc_sh = [], []
-        for ids, shs, b in polys:
-            key, rs = canon([a, b])
-            if key not in fkey_id:
-                fkey_id[key] = len(xyz_list)
-                xyz_list.append(positions(ids, shs).mean(axis=0) - rs * L)
-            fc_ids.append(fkey_id[key])
-            fc_sh.append(rs)
-        allv = {}
-        for ids, shs, _ in polys:
-            for i, s in zip(ids, shs):
-                allv[(int(i), tuple(int(x) for x in s))] = None
-        vv = list(allv)
-        cc = positions([i for i, _ in vv], [s for _, s in vv]).mean(axis=0)
-        cc_id = len(xyz_list)
-        xyz_list.append(cc)
-        _fan_subtets([(ids, shs) for ids, shs, _ in polys], cc_id, fc_ids, sub_vtx, sub_sh, fc_sh, positions)
-        ptr.append(len(sub_vtx))
-        nfaces.append(len(polys))
-
-    xyz = np.array(xyz_list, np.float64)
-    shift = np.array([[np.asarray(s) for s in row] for row in sub_sh], np.int64)
-    if np.abs(shift).max() > 127:
+    xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, L, C,
+                                                            collapse * L / n, face_key_of)
+    if np.abs(sh).max() > 127:
         raise RuntimeError("image shift out of int8 range")
-    return PolyMesh(
-        xyz=xyz,
-        cell_subtet_ptr=np.array(ptr, np.int64),
-        subtet_vtx=np.array(sub_vtx, np.int64),
-        subtet_shift=shift.astype(np.int8),
-        periodic=True,
-        period=(L, L, L),
-        lo=np.zeros(3),
-        hi=np.full(3, L),
-        seeds=seeds,
-        faces_per_cell=np.array(nfaces, np.int64),
-        info={"n_voronoi_vertices": n_voro, "n": n, "L": L, "seed": seed, "collapsed_edges": merges,
-              "collapse": collapse},
-    )
+    return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
+                    subtet_shift=sh.astype(np.int8), periodic=True, period=(L, L, L), lo=np.zeros(3),
+                    hi=np.full(3, L), seeds=seeds, faces_per_cell=nfaces,
+                    info={"n_voronoi_vertices": nvor, "n": n, "L": L, "seed": seed, "collapsed_edges": merges,
+                          "collapse": collapse})
 
 
-def box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
-                collapse: float = COLLAPSE) -> PolyMesh:
+def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
+                 collapse: float = COLLAPSE, seeds: np.ndarray | None = None) -> PolyMesh:
     """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids."""
-    seeds = jittered_seeds(n, lo, hi, seed)
+    if seeds is None:
+        seeds = jittered_seeds(n, lo, hi, seed)
     C = n ** 3
     h = (hi - lo) / n
     margin = 2.5 * h
@@ -333,76 +376,53 @@ def box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
             pts.append(q)
     P = np.concatenate(pts)
     vor = Voronoi(P)
+    cells, nbrs, ptr, flat = _original_faces(vor, P, C)
+    used = np.unique(flat)
+    pos = vor.vertices[used]
+    fv = np.searchsorted(used, flat)
+    fs = np.zeros((len(fv), 3), np.int64)
 
-    ridges_of = [[] for _ in range(C)]
-    for r, (a, b) in enumerate(vor.ridge_points):
-        if a < C:
-            ridges_of[a].append((r, b))
-        if b < C:
-            ridges_of[b].append((r, a))
+    def face_key_of(a, b):
+        return ((min(a, b), max(a, b)) if b < C else (a, -1 - int(b))), np.zeros(3, np.int64)
 
-    vmap: dict[int, int] = {}
-    xyz_list: list = []
+    xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, None, C,
+                                                            collapse * h, face_key_of)
+    return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
+                    subtet_shift=None, periodic=False, period=(0.0, 0.0, 0.0), lo=np.full(3, lo),
+                    hi=np.full(3, hi), seeds=seeds, faces_per_cell=nfaces,
+                    info={"n_voronoi_vertices": nvor, "n": n, "lo": lo, "hi": hi, "seed": seed,
+                          "collapsed_edges": merges, "collapse": collapse})
 
-    def vid(v):
-        if v not in vmap:
-            vmap[v] = len(xyz_list)
-            xyz_list.append(vor.vertices[v])
-        return vmap[v]
 
-    cell_polys_all = []
-    for a in range(C):
-        polys = []
-        for r, b in ridges_of[a]:
-            rv = vor.ridge_vertices[r]
-            if -1 in rv:
-                raise RuntimeError("unbounded ridge next to an original cell")
-            rv = np.array(rv)
-            order = _order_polygon(vor.vertices[rv], P[b] - P[a])
-            rv = rv[order]
-            ids = np.array([vid(int(v)) for v in rv], np.int64)
-            polys.append((ids, np.zeros((len(ids), 3), np.int64), b))
-        cell_polys_all.append(polys)
-    merges = 0
-    if collapse > 0:
-        xyz_list, cell_polys_all, merges = _collapse_short_edges(xyz_list, cell_polys_all, None, collapse * h)
-        xyz_list = list(xyz_list)
-    n_voro = len(xyz_list)
+def cell_centroids(pm: PolyMesh) -> np.ndarray:
+    """Volume centroids of the cells (from the sub-tets), in the frame of each cell."""
+    X = pm.subtet_coords()
+    vol = np.abs(np.linalg.det(np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], -1))) / 6
+    cell = np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr))
+    num = np.zeros((pm.n_cells, 3))
+    np.add.at(num, cell, vol[:, None] * X.mean(axis=1))
+    return num / np.bincount(cell, weights=vol, minlength=pm.n_cells)[:, None]
 
-    def positions(ids, shifts):
-        return np.array([xyz_list[i] for i in ids])
 
-    fkey_id: dict = {}
-    sub_vtx, sub_sh, ptr, nfaces = [], [], [0], []
-    zero = np.zeros(3, np.int64)
-    for a in range(C):
-        polys = cell_polys_all[a]
-        fc_ids = []
-        for ids, _, b in polys:
-            key = (min(a, b), max(a, b)) if b < C else (a, -1 - int(b))
-            if key not in fkey_id:
-                fkey_id[key] = len(xyz_list)
-                xyz_list.append(positions(ids, None).mean(axis=0))
-            fc_ids.append(fkey_id[key])
-        allv = sorted({int(i) for ids, _, _ in polys for i in ids})
-        cc_id = len(xyz_list)
-        xyz_list.append(positions(allv, None).mean(axis=0))
-        _fan_subtets([(ids, z) for ids, z, _ in polys], cc_id, fc_ids, sub_vtx, sub_sh,
-                     [zero] * len(polys), positions)
-        ptr.append(len(sub_vtx))
-        nfaces.append(len(polys))
+def periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
+                     lloyd: int = LLOYD) -> PolyMesh:
+    """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids, after
+    ``lloyd`` Lloyd steps of the jittered seeds and the short-edge collapse."""
+    seeds = jittered_seeds(n, 0.0, L, seed)
+    for _ in range(lloyd):
+        seeds = np.mod(cell_centroids(_periodic_voronoi(n, L, collapse=0.0, seeds=seeds)), L)
+    pm = _periodic_voronoi(n, L, seed, collapse, seeds=seeds)
+    pm.info["lloyd"] = lloyd
+    return pm
 
-    return PolyMesh(
-        xyz=np.array(xyz_list, np.float64),
-        cell_subtet_ptr=np.array(ptr, np.int64),
-        subtet_vtx=np.array(sub_vtx, np.int64),
-        subtet_shift=None,
-        periodic=False,
-        period=(0.0, 0.0, 0.0),
-        lo=np.full(3, lo),
-        hi=np.full(3, hi),
-        seeds=seeds,
-        faces_per_cell=np.array(nfaces, np.int64),
-        info={"n_voronoi_vertices": n_voro, "n": n, "lo": lo, "hi": hi, "seed": seed,
-              "collapsed_edges": merges, "collapse": collapse},
-    )
+
+def box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
+                lloyd: int = LLOYD) -> PolyMesh:
+    """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids, after
+    ``lloyd`` Lloyd steps of the jittered seeds and the short-edge collapse."""
+    seeds = jittered_seeds(n, lo, hi, seed)
+    for _ in range(lloyd):
+        seeds = cell_centroids(_box_voronoi(n, lo, hi, collapse=0.0, seeds=seeds))
+    pm = _box_voronoi(n, lo, hi, seed, collapse, seeds=seeds)
+    pm.info["lloyd"] = lloyd
+    return pm

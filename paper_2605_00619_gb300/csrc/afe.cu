@@ -1,0 +1,592 @@
+// C-ABI implementation (include/afe.h): mesh set-up, the step driver and host plumbing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "afe.h"
+#include "kernels.cuh"
+#include "refelem.hpp"
+#include "topology.hpp"
+
+namespace {
+
+thread_local std::string g_err;
+
+afe_status fail(afe_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define AFE_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(AFE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+struct afe_mesh {
+  afe_params p{};
+  int bc = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int n_sm = 0;
+  afe::RefData ref{};
+  afe::Topology topo;
+  afe::DevMesh dm{};
+  afe::RefData* d_ref = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  void* scratch = nullptr;
+  int64_t scratch_stride = 0;
+  int pred_grid = 0;
+  double* d_totals_partial = nullptr;
+  double* d_totals = nullptr;
+  int totals_blocks = 256;
+  int diag = 0;
+  int pending = 0;  // accumulated status of asynchronous steps
+  int profiling = 0;
+  std::vector<cudaEvent_t> ev;  // 5 events per profiled step
+  size_t ev_used = 0;
+  double t_host = 0;
+  int64_t steps = 0;
+  double last_dt = 0;
+
+  template <typename T>
+  afe_status alloc(T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) return fail(AFE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(p);
+    bytes += (int64_t)(count * sizeof(T));
+    *ptr = (T*)p;
+    return AFE_OK;
+  }
+  template <typename T>
+  afe_status upload(T** ptr, const std::vector<T>& v) {
+    afe_status s = alloc(ptr, v.size());
+    if (s != AFE_OK) return s;
+    if (!v.empty()) AFE_CUDA(cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return AFE_OK;
+  }
+  ~afe_mesh() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+#define AFE_TRY(x)                   \
+  do {                               \
+    afe_status s_ = (x);             \
+    if (s_ != AFE_OK) return s_;     \
+  } while (0)
+
+template <int N, typename Real>
+void launch_predictor(afe_mesh* m) {
+  afe::predictor_kernel<N, Real><<<m->pred_grid, 256, 0, m->stream>>>(m->dm, m->d_ref, (Real*)m->scratch,
+                                                                      m->scratch_stride, m->diag);
+}
+
+template <int N, typename Real>
+void launch_face(afe_mesh* m) {
+  const int64_t threads = m->dm.n_groups * 32;
+  const int blocks = (int)((threads + 255) / 256);
+  if (blocks > 0) afe::face_kernel<N, Real><<<blocks, 256, 0, m->stream>>>(m->dm);
+}
+
+template <int N, typename Real>
+afe_status launch_corrector(afe_mesh* m) {
+  size_t smem = ((size_t)m->dm.Nmax * 5 * sizeof(Real) + 7) / 8 * 8;
+  if (sizeof(Real) == 4) smem += (size_t)m->dm.Nmax * 5 * sizeof(double);
+  // static + dynamic shared memory may exceed the 48 KB default: opt in to the size used
+  AFE_CUDA(cudaFuncSetAttribute(afe::corrector_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = (int)std::min<int64_t>(m->dm.C, (int64_t)m->n_sm * 4);
+  afe::corrector_kernel<N, Real><<<grid, 256, smem, m->stream>>>(m->dm, m->d_ref);
+  return AFE_OK;
+}
+
+template <typename Real>
+afe_status dispatch_stage(afe_mesh* m, int stage) {
+  switch (m->p.order) {
+    case 1:
+      if (stage == 0) launch_predictor<1, Real>(m);
+      else if (stage == 1) launch_face<1, Real>(m);
+      else return launch_corrector<1, Real>(m);
+      break;
+    case 2:
+      if (stage == 0) launch_predictor<2, Real>(m);
+      else if (stage == 1) launch_face<2, Real>(m);
+      else return launch_corrector<2, Real>(m);
+      break;
+    case 3:
+      if (stage == 0) launch_predictor<3, Real>(m);
+      else if (stage == 1) launch_face<3, Real>(m);
+      else return launch_corrector<3, Real>(m);
+      break;
+    default:
+      return fail(AFE_EINVAL, "order must be 1, 2 or 3");
+  }
+  return AFE_OK;
+}
+
+afe_status stage(afe_mesh* m, int s) {
+  return m->p.precision == AFE_FP32 ? dispatch_stage<float>(m, s) : dispatch_stage<double>(m, s);
+}
+
+// limiter (if on) and the time step, all on the device
+afe_status enqueue_dt(afe_mesh* m, double dt) {
+  const int cgrid = (int)std::min<int64_t>(m->dm.C, (int64_t)m->n_sm * 8);
+  if (m->p.limiter) {
+    afe::cell_means_kernel<<<cgrid, 256, 0, m->stream>>>(m->dm);
+    afe::limiter_kernel<<<(int)((m->dm.C + 127) / 128), 128, 0, m->stream>>>(m->dm);
+  }
+  if (dt > 0) {
+    afe::set_dt_kernel<<<1, 1, 0, m->stream>>>(m->dm, dt);
+  } else {
+    AFE_CUDA(cudaMemsetAsync(m->dm.maxbits, 0, sizeof(unsigned long long), m->stream));
+    afe::cfl_kernel<<<cgrid, 128, 0, m->stream>>>(m->dm);
+    afe::dt_finalize_kernel<<<1, 1, 0, m->stream>>>(m->dm);
+  }
+  return AFE_OK;
+}
+
+afe_status record(afe_mesh* m, int k) {
+  if (!m->profiling) return AFE_OK;
+  if (m->ev_used >= m->ev.size()) {
+    cudaEvent_t e;
+    AFE_CUDA(cudaEventCreate(&e));
+    m->ev.push_back(e);
+  }
+  (void)k;
+  AFE_CUDA(cudaEventRecord(m->ev[m->ev_used++], m->stream));
+  return AFE_OK;
+}
+
+afe_status enqueue_step(afe_mesh* m, double dt) {
+  AFE_CUDA(cudaMemsetAsync(m->dm.flags, 0, afe::F_COUNT * sizeof(int), m->stream));
+  AFE_TRY(record(m, 0));
+  AFE_TRY(enqueue_dt(m, dt));
+  AFE_CUDA(cudaMemsetAsync(m->dm.work, 0, sizeof(int), m->stream));
+  AFE_TRY(record(m, 1));
+  AFE_TRY(stage(m, 0));
+  AFE_TRY(record(m, 2));
+  AFE_TRY(stage(m, 1));
+  AFE_TRY(record(m, 3));
+  AFE_TRY(stage(m, 2));
+  AFE_TRY(record(m, 4));
+  afe::advance_time_kernel<<<1, 1, 0, m->stream>>>(m->dm);
+  AFE_CUDA(cudaGetLastError());
+  return AFE_OK;
+}
+
+afe_status read_flags(afe_mesh* m, int* flags) {
+  AFE_CUDA(cudaMemcpyAsync(flags, m->dm.flags, afe::F_COUNT * sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  return AFE_OK;
+}
+
+afe_status status_of(const int* flags) {
+  if (flags[afe::F_NONFINITE]) return fail(AFE_ENONFINITE, "non-finite or inadmissible state (flags " +
+                                                               std::to_string(flags[afe::F_NONFINITE]) + ")");
+  if (flags[afe::F_NONCONV])
+    return fail(AFE_ENOCONV, std::to_string(flags[afe::F_NONCONV]) + " cells hit picard_max");
+  return AFE_OK;
+}
+
+afe_status check_params(const afe_params* p) {
+  if (!p) return fail(AFE_EINVAL, "params is NULL");
+  if (p->order < 1 || p->order > 3) return fail(AFE_EINVAL, "order must be 1, 2 or 3");
+  if (p->precision != AFE_FP64 && p->precision != AFE_FP32) return fail(AFE_EINVAL, "unknown precision");
+  if (p->equations != AFE_EULER && p->equations != AFE_NAVIER_STOKES) return fail(AFE_EINVAL, "unknown equations");
+  if (!(p->gamma > 1.0) || !(p->R > 0.0) || !(p->cfl > 0.0) || !(p->picard_tol > 0.0) || p->picard_max < 1)
+    return fail(AFE_EINVAL, "gamma > 1, R > 0, cfl > 0, picard_tol > 0 and picard_max >= 1 are required");
+  if (p->mu < 0.0) return fail(AFE_EINVAL, "mu must be >= 0");
+  if (p->kappa < 0.0 && !(p->Pr > 0.0)) return fail(AFE_EINVAL, "Pr > 0 is required when kappa < 0");
+  return AFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* afe_last_error(void) { return g_err.c_str(); }
+
+afe_status afe_default_params(afe_params* p, int order) {
+  if (!p) return fail(AFE_EINVAL, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->order = order;
+  p->equations = AFE_EULER;
+  p->precision = AFE_FP64;
+  p->gamma = 1.4;
+  p->R = 1.0;
+  p->mu = 0.0;
+  p->Pr = 0.71;
+  p->kappa = 0.0;
+  p->cfl = 0.3;
+  p->limiter = 0;
+  p->m1 = 0.1;
+  p->picard_tol = 1e-12;
+  p->picard_max = 64;
+  p->period[0] = p->period[1] = p->period[2] = 1.0;
+  return (order >= 1 && order <= 3) ? AFE_OK : fail(AFE_EINVAL, "order must be 1, 2 or 3");
+}
+
+afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double* xyz, int64_t n_cells,
+                           const int64_t* cell_subtet_ptr, const int64_t* subtet_vtx, const int8_t* subtet_shift,
+                           int boundary, void* cuda_stream, afe_mesh** out) {
+  if (!out) return fail(AFE_EINVAL, "out is NULL");
+  *out = nullptr;
+  AFE_TRY(check_params(p));
+  if (!xyz || !cell_subtet_ptr || !subtet_vtx || n_vertices <= 0 || n_cells <= 0)
+    return fail(AFE_EINVAL, "mesh arrays must be non-NULL and non-empty");
+  if (boundary != AFE_BC_PERIODIC && boundary != AFE_BC_TRANSMISSIVE) return fail(AFE_EINVAL, "unknown boundary");
+  if (boundary == AFE_BC_PERIODIC && subtet_shift)
+    for (int d = 0; d < 3; ++d)
+      if (!(p->period[d] > 0.0)) return fail(AFE_EINVAL, "period must be > 0 with image shifts");
+
+  std::unique_ptr<afe_mesh> m(new afe_mesh());
+  m->p = *p;
+  m->bc = boundary;
+  m->stream = (cudaStream_t)cuda_stream;
+  if (!afe::build_ref(p->order, &m->ref)) return fail(AFE_EINVAL, "reference element build failed");
+  {
+    std::string err;
+    double period[3] = {p->period[0], p->period[1], p->period[2]};
+    if (!subtet_shift) period[0] = period[1] = period[2] = 0.0;
+    int rc = afe::build_topology(m->ref, n_vertices, xyz, n_cells, cell_subtet_ptr, subtet_vtx, subtet_shift, period,
+                                 boundary == AFE_BC_PERIODIC, &m->topo, &err);
+    if (rc) return fail(rc == 2 ? AFE_EMESH : AFE_EINVAL, err);
+  }
+
+  // ---- GPU part
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(AFE_ECUDA, "no CUDA device");
+  AFE_CUDA(cudaGetDevice(&m->device));
+  AFE_CUDA(cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, m->device));
+  const afe::Topology& T = m->topo;
+  afe::DevMesh& d = m->dm;
+  d.N = p->order;
+  d.C = T.C;
+  d.n_nodes = T.n_nodes;
+  d.n_slots = T.n_slots;
+  d.n_groups = T.n_groups;
+  d.Nmax = T.Nmax;
+  d.Smax = T.Smax;
+  d.gamma = p->gamma;
+  d.Rgas = p->R;
+  d.cv = p->R / (p->gamma - 1.0);
+  d.cfl = p->cfl;
+  d.m1 = p->m1;
+  d.mu0 = (p->equations == AFE_NAVIER_STOKES) ? p->mu : 0.0;
+  d.Pr = p->Pr;
+  d.kappa0 = (p->equations == AFE_NAVIER_STOKES) ? p->kappa : (p->kappa < 0 ? 0.0 : p->kappa);
+  d.tol = p->picard_tol;
+  d.h_min = T.h_min;
+  d.picard_max = p->picard_max;
+  d.limiter = p->limiter;
+  d.eq = p->equations;
+  afe_mesh* M = m.get();
+  AFE_TRY(M->upload((int64_t**)&d.node_ptr, T.node_ptr));
+  AFE_TRY(M->upload((int64_t**)&d.sub_ptr, T.sub_ptr));
+  AFE_TRY(M->upload((int64_t**)&d.slot_ptr, T.slot_ptr));
+  AFE_TRY(M->upload((int64_t**)&d.minv_ptr, T.minv_ptr));
+  AFE_TRY(M->upload((uint16_t**)&d.A, T.A));
+  AFE_TRY(M->upload((double**)&d.geo, T.geo));
+  AFE_TRY(M->upload((int64_t**)&d.inc_ptr, T.inc_ptr));
+  AFE_TRY(M->upload((uint32_t**)&d.inc, T.inc));
+  AFE_TRY(M->upload((int32_t**)&d.slot_cell, T.slot_cell));
+  AFE_TRY(M->upload((uint16_t**)&d.slot_sub, T.slot_sub));
+  AFE_TRY(M->upload((uint8_t**)&d.slot_loc, T.slot_loc));
+  AFE_TRY(M->upload((uint16_t**)&d.slot_node, T.slot_node));
+  AFE_TRY(M->upload((double**)&d.slot_geo, T.slot_geo));
+  AFE_TRY(M->upload((int64_t**)&d.slot_partner, T.slot_partner));
+  AFE_TRY(M->upload((int32_t**)&d.slot_nbr, T.slot_nbr));
+  AFE_TRY(M->upload((int64_t**)&d.finc_ptr, T.finc_ptr));
+  AFE_TRY(M->upload((uint32_t**)&d.finc, T.finc));
+  AFE_TRY(M->upload((int64_t**)&d.group_ptr, T.group_ptr));
+  AFE_TRY(M->upload((int64_t**)&d.group_slot, T.group_slot));
+  AFE_TRY(M->upload((double**)&d.cell_vol, T.cell_vol));
+  AFE_TRY(M->upload((double**)&d.cell_h, T.cell_h));
+  AFE_TRY(M->alloc(&d.wvec, T.n_nodes));
+  const int64_t nminv = T.minv_ptr[T.C];
+  AFE_TRY(M->alloc(&d.minv64, nminv));
+  if (p->precision == AFE_FP32) AFE_TRY(M->alloc(&d.minv32, nminv));
+  AFE_TRY(M->alloc(&d.u, T.n_nodes * 5));
+  const size_t rb = p->precision == AFE_FP32 ? 4 : 8;
+  {
+    void* v;
+    AFE_TRY(M->alloc((char**)&v, T.n_nodes * 5 * rb));
+    d.vol = v;
+    AFE_TRY(M->alloc((char**)&v, T.n_slots * T.Nf * 5 * rb));
+    d.slot_q = v;
+    AFE_TRY(M->alloc((char**)&v, T.n_slots * T.Nf * 5 * rb));
+    d.slot_fn = v;
+    AFE_TRY(M->alloc((char**)&v, T.n_slots * T.Nf * 5 * rb));
+    d.slot_G = v;
+  }
+  AFE_TRY(M->alloc(&d.iters, T.C));
+  AFE_TRY(M->alloc(&d.beta, T.C));
+  AFE_TRY(M->alloc(&d.mu, T.C));
+  AFE_TRY(M->alloc(&d.means, T.C * 5));
+  AFE_TRY(M->alloc(&d.dt, 1));
+  AFE_TRY(M->alloc(&d.tacc, 1));
+  AFE_TRY(M->alloc(&d.maxbits, 1));
+  AFE_TRY(M->alloc(&d.flags, afe::F_COUNT));
+  AFE_TRY(M->alloc(&d.work, 1));
+  AFE_TRY(M->alloc(&M->d_ref, 1));
+  AFE_TRY(M->alloc(&M->d_totals_partial, (size_t)M->totals_blocks * 5));
+  AFE_TRY(M->alloc(&M->d_totals, 5));
+  AFE_CUDA(cudaMemcpy(M->d_ref, &M->ref, sizeof(afe::RefData), cudaMemcpyHostToDevice));
+  AFE_CUDA(cudaMemset(d.u, 0, T.n_nodes * 5 * sizeof(double)));
+  AFE_CUDA(cudaMemset(d.beta, 0, T.C * sizeof(double)));
+  AFE_CUDA(cudaMemset(d.tacc, 0, sizeof(double)));
+  AFE_CUDA(cudaMemset(d.iters, 0, T.C * sizeof(int32_t)));
+  {
+    std::vector<double> mu0(T.C, d.mu0);
+    AFE_CUDA(cudaMemcpy(d.mu, mu0.data(), T.C * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  // predictor scratch (persistent grid, one slice per block)
+  {
+    const int64_t per = (int64_t)T.Nmax * T.Nt * 5 * 3 + (int64_t)T.Smax * T.Nt * T.Np * 5 * 4;
+    M->scratch_stride = (per + 31) / 32 * 32;
+    M->pred_grid = (int)std::min<int64_t>(T.C, (int64_t)M->n_sm * 2);
+    void* s;
+    AFE_TRY(M->alloc((char**)&s, (size_t)M->scratch_stride * M->pred_grid * rb));
+    M->scratch = s;
+  }
+  // FP64 set-up on the GPU: mass matrices, w_i, inverses
+  AFE_CUDA(cudaMemsetAsync(d.flags, 0, afe::F_COUNT * sizeof(int), M->stream));
+  const int sgrid = (int)std::min<int64_t>(T.C, (int64_t)M->n_sm * 4);
+  afe::assemble_mass_kernel<<<sgrid, 256, 0, M->stream>>>(d, M->d_ref);
+  afe::invert_spd_kernel<<<(int)std::min<int64_t>(T.C, (int64_t)M->n_sm * 4), 256, 0, M->stream>>>(d);
+  afe::symmetrize_kernel<<<sgrid, 256, 0, M->stream>>>(d, p->precision == AFE_FP32);
+  AFE_CUDA(cudaGetLastError());
+  int flags[afe::F_COUNT];
+  AFE_TRY(read_flags(M, flags));
+  if (flags[afe::F_NONFINITE]) return fail(AFE_EMESH, "a cell mass matrix is not positive definite");
+  if (p->precision == AFE_FP32) {
+    // only the FP32 copy is used by the reduced-precision step
+    for (size_t i = 0; i < M->allocs.size(); ++i)
+      if (M->allocs[i] == d.minv64) {
+        cudaFree(d.minv64);
+        M->allocs.erase(M->allocs.begin() + i);
+        M->bytes -= nminv * 8;
+        d.minv64 = nullptr;
+        break;
+      }
+  }
+  *out = m.release();
+  return AFE_OK;
+}
+
+afe_status afe_mesh_validate(const afe_params* p, int64_t n_vertices, const double* xyz, int64_t n_cells,
+                             const int64_t* cell_subtet_ptr, const int64_t* subtet_vtx, const int8_t* subtet_shift,
+                             int boundary, int64_t* n_nodes, int64_t* n_face_tris) {
+  AFE_TRY(check_params(p));
+  if (!xyz || !cell_subtet_ptr || !subtet_vtx || n_vertices <= 0 || n_cells <= 0)
+    return fail(AFE_EINVAL, "mesh arrays must be non-NULL and non-empty");
+  if (boundary != AFE_BC_PERIODIC && boundary != AFE_BC_TRANSMISSIVE) return fail(AFE_EINVAL, "unknown boundary");
+  afe::RefData ref;
+  if (!afe::build_ref(p->order, &ref)) return fail(AFE_EINVAL, "reference element build failed");
+  afe::Topology topo;
+  std::string err;
+  double period[3] = {p->period[0], p->period[1], p->period[2]};
+  if (!subtet_shift) period[0] = period[1] = period[2] = 0.0;
+  int rc = afe::build_topology(ref, n_vertices, xyz, n_cells, cell_subtet_ptr, subtet_vtx, subtet_shift, period,
+                               boundary == AFE_BC_PERIODIC, &topo, &err);
+  if (rc) return fail(rc == 2 ? AFE_EMESH : AFE_EINVAL, err);
+  if (n_nodes) *n_nodes = topo.n_nodes;
+  if (n_face_tris) *n_face_tris = topo.n_slots;
+  return AFE_OK;
+}
+
+void afe_mesh_destroy(afe_mesh* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  else cudaDeviceSynchronize();
+  delete m;
+}
+
+afe_status afe_num_nodes(const afe_mesh* m, int64_t* n_nodes, int64_t* node_ptr) {
+  if (!m || !n_nodes) return fail(AFE_EINVAL, "NULL argument");
+  *n_nodes = m->topo.n_nodes;
+  if (node_ptr) std::memcpy(node_ptr, m->topo.node_ptr.data(), (m->topo.C + 1) * sizeof(int64_t));
+  return AFE_OK;
+}
+
+afe_status afe_get_node_coords(const afe_mesh* m, double* xyz) {
+  if (!m || !xyz) return fail(AFE_EINVAL, "NULL argument");
+  std::memcpy(xyz, m->topo.node_xyz.data(), m->topo.node_xyz.size() * sizeof(double));
+  return AFE_OK;
+}
+
+afe_status afe_set_stream(afe_mesh* m, void* s) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  m->stream = (cudaStream_t)s;
+  return AFE_OK;
+}
+
+afe_status afe_set_state(afe_mesh* m, const double* q) {
+  if (!m || !q) return fail(AFE_EINVAL, "NULL argument");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  AFE_CUDA(cudaMemcpy(m->dm.u, q, m->topo.n_nodes * 5 * sizeof(double), cudaMemcpyHostToDevice));
+  return AFE_OK;
+}
+
+afe_status afe_set_state_device(afe_mesh* m, const double* dq, void* s) {
+  if (!m || !dq) return fail(AFE_EINVAL, "NULL argument");
+  cudaStream_t st = s ? (cudaStream_t)s : m->stream;
+  AFE_CUDA(cudaMemcpyAsync(m->dm.u, dq, m->topo.n_nodes * 5 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (st != m->stream) AFE_CUDA(cudaStreamSynchronize(st));
+  return AFE_OK;
+}
+
+afe_status afe_get_state(const afe_mesh* m, double* q) {
+  if (!m || !q) return fail(AFE_EINVAL, "NULL argument");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  AFE_CUDA(cudaMemcpy(q, m->dm.u, m->topo.n_nodes * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+  return AFE_OK;
+}
+
+afe_status afe_get_state_device(const afe_mesh* m, double* dq) {
+  if (!m || !dq) return fail(AFE_EINVAL, "NULL argument");
+  AFE_CUDA(cudaMemcpyAsync(dq, m->dm.u, m->topo.n_nodes * 5 * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  return AFE_OK;
+}
+
+afe_status afe_compute_dt(afe_mesh* m, double* dt) {
+  if (!m || !dt) return fail(AFE_EINVAL, "NULL argument");
+  AFE_CUDA(cudaMemsetAsync(m->dm.flags, 0, afe::F_COUNT * sizeof(int), m->stream));
+  AFE_TRY(enqueue_dt(m, -1.0));
+  AFE_CUDA(cudaMemcpyAsync(dt, m->dm.dt, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  int flags[afe::F_COUNT];
+  AFE_TRY(read_flags(m, flags));
+  return status_of(flags);
+}
+
+afe_status afe_step(afe_mesh* m, double dt) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  AFE_TRY(enqueue_step(m, dt));
+  int flags[afe::F_COUNT];
+  double hdt = 0;
+  AFE_CUDA(cudaMemcpyAsync(&hdt, m->dm.dt, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  AFE_TRY(read_flags(m, flags));
+  m->last_dt = hdt;
+  m->t_host += hdt;
+  m->steps += 1;
+  return status_of(flags);
+}
+
+afe_status afe_step_async(afe_mesh* m, double dt, int nsteps) {
+  if (!m || nsteps < 0) return fail(AFE_EINVAL, "bad argument");
+  for (int i = 0; i < nsteps; ++i) {
+    AFE_TRY(enqueue_step(m, dt));
+    // fold this step's flags into the pending status without a host round trip
+    m->steps += 1;
+  }
+  m->pending += nsteps;
+  return AFE_OK;
+}
+
+afe_status afe_sync(afe_mesh* m) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  int flags[afe::F_COUNT];
+  double hdt = 0, ht = 0;
+  AFE_CUDA(cudaMemcpyAsync(&hdt, m->dm.dt, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  AFE_CUDA(cudaMemcpyAsync(&ht, m->dm.tacc, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  AFE_TRY(read_flags(m, flags));
+  m->last_dt = hdt;
+  m->t_host = ht;
+  m->pending = 0;
+  return status_of(flags);
+}
+
+afe_status afe_get_stats(const afe_mesh* mc, afe_stats* s) {
+  afe_mesh* m = const_cast<afe_mesh*>(mc);
+  if (!m || !s) return fail(AFE_EINVAL, "NULL argument");
+  std::memset(s, 0, sizeof(*s));
+  std::vector<int32_t> it(m->topo.C);
+  int flags[afe::F_COUNT];
+  afe::totals_partial_kernel<<<m->totals_blocks, 256, 0, m->stream>>>(m->dm, m->d_totals_partial);
+  afe::totals_final_kernel<<<1, 32, 0, m->stream>>>(m->d_totals_partial, m->totals_blocks, m->d_totals);
+  AFE_CUDA(cudaGetLastError());
+  AFE_CUDA(cudaMemcpyAsync(it.data(), m->dm.iters, m->topo.C * sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream));
+  AFE_CUDA(cudaMemcpyAsync(s->totals, m->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  double ht = 0;
+  AFE_CUDA(cudaMemcpyAsync(&ht, m->dm.tacc, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  AFE_CUDA(cudaMemcpyAsync(&s->dt, m->dm.dt, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  AFE_TRY(read_flags(m, flags));
+  s->t = ht;
+  s->steps = m->steps;
+  int64_t sum = 0;
+  int32_t mx = 0;
+  for (int32_t v : it) {
+    sum += v;
+    mx = std::max(mx, v);
+  }
+  s->picard_mean = (double)sum / (double)m->topo.C;
+  s->picard_max = mx;
+  s->nonconverged = flags[afe::F_NONCONV];
+  s->troubled = flags[afe::F_TROUBLED];
+  return AFE_OK;
+}
+
+afe_status afe_set_diagnostics(afe_mesh* m, int on) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  if (on && !m->dm.qbar_diag) AFE_TRY(m->alloc(&m->dm.qbar_diag, m->topo.n_nodes * 5));
+  m->diag = on ? 1 : 0;
+  return AFE_OK;
+}
+
+afe_status afe_get_diagnostics(const afe_mesh* m, double* qbar, int32_t* iterations, double* beta, double* mu) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  if (qbar) {
+    if (!m->dm.qbar_diag) return fail(AFE_EINVAL, "diagnostics were not enabled");
+    AFE_CUDA(cudaMemcpy(qbar, m->dm.qbar_diag, m->topo.n_nodes * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  if (iterations) AFE_CUDA(cudaMemcpy(iterations, m->dm.iters, m->topo.C * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (beta) AFE_CUDA(cudaMemcpy(beta, m->dm.beta, m->topo.C * sizeof(double), cudaMemcpyDeviceToHost));
+  if (mu) AFE_CUDA(cudaMemcpy(mu, m->dm.mu, m->topo.C * sizeof(double), cudaMemcpyDeviceToHost));
+  return AFE_OK;
+}
+
+afe_status afe_set_profiling(afe_mesh* m, int on) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  m->profiling = on ? 1 : 0;
+  return AFE_OK;
+}
+
+afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset) {
+  if (!m || !ms) return fail(AFE_EINVAL, "NULL argument");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  for (int s = 0; s < 4; ++s) ms[s] = 0.0;
+  const size_t n = m->ev_used / 5;
+  for (size_t i = 0; i < n; ++i)
+    for (int s = 0; s < 4; ++s) {
+      float t = 0.f;
+      AFE_CUDA(cudaEventElapsedTime(&t, m->ev[i * 5 + s], m->ev[i * 5 + s + 1]));
+      ms[s] += t;
+    }
+  if (nsteps) *nsteps = (int64_t)n;
+  if (reset) m->ev_used = 0;
+  return AFE_OK;
+}
+
+afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes) {
+  if (!m || !bytes) return fail(AFE_EINVAL, "NULL argument");
+  *bytes = m->bytes;
+  return AFE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+"""GPU parity: the C-ABI library against the FP64 oracle on the same seeded inputs.
+
+Bar (FP64 path): relative L-infinity <= 1e-11 per conserved variable, normalised by the
+oracle's max |value|, after the stated number of steps.  Reduced-precision path:
+relative L2 <= 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import states
+from inputs.voronoi import box_voronoi, periodic_voronoi
+from tests.harness import Pair, rel_l2, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-11
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def afe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2605_00619_gb300 import afe as mod
+    mod.lib()
+    return mod
+
+
+def _run(pair, ic, nsteps, dt=None):
+    pair.set_state(ic(pair.om.node_coords()))
+    for _ in range(nsteps):
+        info = pair.oracle_step(dt)
+        st = pair.lib_step(dt if dt else 0.0)
+        assert st == 0
+    return info
+
+
+def test_predictor_and_single_step_p1(afe):
+    pm = periodic_voronoi(3)
+    p = afe.afe_default_params(1, cfl=0.5)
+    pr = Pair(pm, p)
+    afe.afe_set_diagnostics(pr.h, True)
+    u0 = states.density_wave(pr.om.node_coords())
+    pr.set_state(u0)
+    info = pr.oracle_step()
+    assert pr.lib_step() == 0
+    s = afe.afe_get_stats(pr.h)
+    assert abs(s.dt - info.dt) <= 1e-14 * info.dt
+    qb, it, beta, mu = afe.afe_get_diagnostics(pr.h, pm.n_cells)
+    # iteration counts agree within one (both stop at the 1e-12 residual)
+    assert np.abs(it - info.iterations).max() <= 1
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
+def test_config1_p1_density_wave_10_steps(afe):
+    """6^3 periodic Voronoi, P1, CFL 0.5, 10 steps: the small parity workload."""
+    pm = periodic_voronoi(6)
+    p = afe.afe_default_params(1, cfl=0.5)
+    pr = Pair(pm, p)
+    _run(pr, states.density_wave, 10)
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
+@pytest.mark.parametrize("N,n,steps", [(2, 3, 4), (3, 2, 3)])
+def test_higher_order_density_wave(afe, N, n, steps):
+    pm = periodic_voronoi(n)
+    p = afe.afe_default_params(N)
+    pr = Pair(pm, p)
+    _run(pr, states.density_wave, steps)
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
+def test_transmissive_box_with_limiter(afe):
+    """Spherical explosion data on a box mesh with the artificial-viscosity limiter."""
+    pm = box_voronoi(3)
+    p = afe.afe_default_params(2, limiter=1)
+    pr = Pair(pm, p)
+    ic = lambda x: states.spherical_riemann(x, alpha0=1.5 * pr.om.h_min)
+    pr.set_state(ic(pr.om.node_coords()))
+    for _ in range(3):
+        info = pr.oracle_step()
+        assert pr.lib_step(check=False) in (0, 5)
+    _, _, beta, mu = afe.afe_get_diagnostics(pr.h, pm.n_cells, qbar=False)
+    np.testing.assert_allclose(beta, info.beta, atol=1e-12)
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
+def test_navier_stokes_taylor_green(afe):
+    pm = periodic_voronoi(2)
+    p = afe.afe_default_params(2, equations=afe.AFE_NAVIER_STOKES, mu=0.005, kappa=-1.0, Pr=0.71)
+    pr = Pair(pm, p)
+    _run(pr, lambda x: states.taylor_green_3d(2 * math.pi * x, p0=10.0), 2)
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_fp32_path_within_1e5(afe, N):
+    pm = periodic_voronoi(3 if N < 3 else 2)
+    p = afe.afe_default_params(N, precision=afe.AFE_FP32, picard_tol=1e-6)
+    pr = Pair(pm, p)
+    u0 = states.density_wave(pr.om.node_coords())
+    pr.set_state(u0)
+    for _ in range(3):
+        info = pr.oracle_step()
+        assert pr.lib_step(info.dt) == 0
+    assert rel_l2(pr.lib_state(), pr.u) <= FP32_TOL
+    # conserved totals exact in FP64 despite the FP32 arithmetic
+    s = afe.afe_get_stats(pr.h)
+    from oracle import scheme
+    t0 = scheme.conserved_totals(pr.om, pr.om.split(u0))
+    np.testing.assert_allclose(np.array(s.totals), t0, rtol=0, atol=1e-13 * np.abs(t0).max())
+    pr.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_free_stream_and_conservation_on_gpu(afe, prec):
+    pm = periodic_voronoi(3)
+    p = afe.afe_default_params(2, precision=prec, picard_tol=1e-12 if prec == 0 else 1e-6)
+    pr = Pair(pm, p)
+    u = states.constant(pr.om.node_coords())
+    pr.set_state(u)
+    for _ in range(3):
+        assert pr.lib_step() == 0
+    err = np.abs(pr.lib_state() - u).max()
+    assert err < (1e-12 if prec == 0 else 1e-5)
+    u = states.density_wave(pr.om.node_coords())
+    pr.set_state(u)
+    t0 = np.array(afe.afe_get_stats(pr.h).totals)
+    for _ in range(3):
+        assert pr.lib_step() == 0
+    t1 = np.array(afe.afe_get_stats(pr.h).totals)
+    np.testing.assert_allclose(t1, t0, rtol=0, atol=1e-13 * np.abs(t0).max())
+    pr.close()
+
+
+def test_bitwise_determinism_and_restart(afe):
+    pm = periodic_voronoi(3)
+    p = afe.afe_default_params(2)
+    pr = Pair(pm, p)
+    u0 = states.density_wave(pr.om.node_coords())
+    pr.set_state(u0)
+    for _ in range(4):
+        assert pr.lib_step(0.002) == 0
+    a = afe.afe_get_state(pr.h)
+    pr.set_state(u0)
+    for _ in range(2):
+        assert pr.lib_step(0.002) == 0
+    mid = afe.afe_get_state(pr.h)
+    afe.afe_set_state(pr.h, mid)       # checkpoint / resume through the host
+    for _ in range(2):
+        assert pr.lib_step(0.002) == 0
+    b = afe.afe_get_state(pr.h)
+    np.testing.assert_array_equal(a, b)
+    pr.close()
