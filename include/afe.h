@@ -81,6 +81,7 @@ typedef struct {
   int64_t nonconverged; /* cells that hit picard_max, last step                  */
   int64_t troubled;     /* cells with beta_i > 0, last step                      */
   double totals[5];     /* sum_i 1^T M_i u_i per conserved variable (FP64)       */
+  int64_t kernel_launches; /* kernels launched by afe_step / afe_step_async so far */
 } afe_stats;
 
 typedef struct afe_mesh afe_mesh; /* opaque; owns all device memory of one simulation */

@@ -25,8 +25,10 @@ Recipe
   generator (Sec. 3).  A merge that would fold a sub-tet is skipped.
 * Lloyd step: before the tessellation used, each jittered seed is moved once to
   the volume centroid of its own Voronoi cell.  Together with the collapse this
-  removes the thin faces and needle sub-tets that otherwise leave a few cells per
+  removes most thin faces and needle sub-tets that otherwise leave a few cells per
   thousand with a divergent predictor iteration at CFL 0.3.
+* Thin faces: a face whose centre lies closer than ``THIN`` times the lattice
+  spacing to the line of one of its edges has its shortest edge collapsed too.
 * Fan subgrid: each cell is split by joining its centre (the mean of its
   vertices) to a fan triangulation of each face about the face centre (the mean
   of the face's vertices): one sub-tet per face edge.
@@ -48,6 +50,9 @@ from scipy.spatial import Voronoi
 JITTER = 0.3
 # Voronoi edges shorter than COLLAPSE * (lattice spacing) are collapsed
 COLLAPSE = 0.2
+# fan triangles whose face centre is closer than THIN * (lattice spacing) to their edge
+# mark a thin face; its shortest edge is collapsed too
+THIN = 0.04
 # Lloyd steps applied to the jittered seeds (each moves a seed to its cell's centroid)
 LLOYD = 1
 
@@ -139,7 +144,7 @@ def _next_index(ptr):
     return nxt
 
 
-def _collapse(pos, ptr, fv, fs, L, tol, exclude):
+def _collapse(pos, ptr, fv, fs, L, tol, exclude, force=()):
     """Union-find merge of the end points of Voronoi edges shorter than tol.
 
     pos: canonical vertex positions [nv, 3]; (ptr, fv, fs): per face the vertex ids and their
@@ -148,35 +153,48 @@ def _collapse(pos, ptr, fv, fs, L, tol, exclude):
     of each merged vertex.
     """
     nv = len(pos)
-    parent = np.arange(nv)
-    off = np.zeros((nv, 3), np.int64)
     Lf = 0.0 if L is None else L
     nxt = _next_index(ptr)
     P = pos[fv] + fs * Lf
     d = np.linalg.norm(P - P[nxt], axis=1)
 
+    par = list(range(nv))
+    ofs = [(0, 0, 0)] * nv
+
     def find(x):
-        o = np.zeros(3, np.int64)
-        while parent[x] != x:
-            o = o + off[x]
-            x = parent[x]
-        return x, o
+        o0 = o1 = o2 = 0
+        while par[x] != x:
+            a = ofs[x]
+            o0 += a[0]
+            o1 += a[1]
+            o2 += a[2]
+            x = par[x]
+        return x, (o0, o1, o2)
 
     merges = 0
-    for e in np.nonzero(d < tol)[0]:
-        a, b = int(fv[e]), int(fv[nxt[e]])
+    cand = d < tol
+    if len(force):
+        cand[np.asarray(sorted(force), np.int64)] = True
+    fvl = fv.tolist()
+    fsl = [tuple(r) for r in fs.tolist()]
+    nxl = nxt.tolist()
+    for e in np.nonzero(cand)[0].tolist():
+        a, b = fvl[e], fvl[nxl[e]]
         if a in exclude or b in exclude:
             continue
         ra, oa = find(a)
         rb, ob = find(b)
-        rel = oa + fs[e] - ob - fs[nxt[e]]
+        sa, sb = fsl[e], fsl[nxl[e]]
+        rel = (oa[0] + sa[0] - ob[0] - sb[0], oa[1] + sa[1] - ob[1] - sb[1], oa[2] + sa[2] - ob[2] - sb[2])
         if ra == rb:
-            if np.any(rel != 0):
+            if rel != (0, 0, 0):
                 raise RuntimeError("short-edge cluster wraps around the period")
             continue
-        parent[rb] = ra
-        off[rb] = rel
+        par[rb] = ra
+        ofs[rb] = rel
         merges += 1
+    parent = np.asarray(par, np.int64)
+    off = np.asarray(ofs, np.int64).reshape(nv, 3)
     # pointer jumping: root of every vertex and its image offset relative to the root
     p = parent.copy()
     roff = off.copy()
@@ -212,7 +230,7 @@ def _collapse(pos, ptr, fv, fs, L, tol, exclude):
     keep_e &= keep_f[fidx]
     cnt3 = cnt2[keep_f]
     ptr2 = np.concatenate([[0], np.cumsum(cnt3)])
-    return new_pos, ptr2, ids[keep_e], sh[keep_e], np.nonzero(keep_f)[0], merges, members
+    return new_pos, ptr2, ids[keep_e], sh[keep_e], np.nonzero(keep_f)[0], merges, members, new_id
 
 
 def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
@@ -222,18 +240,12 @@ def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
     X = pos[fv] + fs * Lf
     fpos = np.add.reduceat(X, ptr[:-1], axis=0) / cnt[:, None]
     # face centres: one vertex per face pair, in a canonical frame
-    key_id: dict = {}
-    extra = []
     nf = len(cnt)
-    fc_id = np.empty(nf, np.int64)
-    fc_sh = np.empty((nf, 3), np.int64)
-    for f in range(nf):
-        key, rs = face_key(f)
-        if key not in key_id:
-            key_id[key] = len(pos) + len(extra)
-            extra.append(fpos[f] - rs * Lf)
-        fc_id[f] = key_id[key]
-        fc_sh[f] = rs
+    krows, fc_sh = face_key(np.arange(nf))
+    _, first, inv = np.unique(krows, axis=0, return_index=True, return_inverse=True)
+    inv = inv.ravel()
+    extra = fpos[first] - fc_sh[first] * Lf
+    fc_id = len(pos) + inv
     fidx = np.repeat(np.arange(nf), cnt)
     fcell = cells[fidx]
     # cell centres: mean of the distinct vertices of each cell
@@ -244,7 +256,7 @@ def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
     np.add.at(csum, u[:, 0], upos)
     ccen = csum / np.bincount(u[:, 0], minlength=C)[:, None]
     cc_id = len(pos) + len(extra) + np.arange(C)
-    xyz = np.concatenate([pos, np.asarray(extra).reshape(-1, 3), ccen])
+    xyz = np.concatenate([pos, extra, ccen])
     # fan sub-tets (cell centre, face centre, v_i, v_i+1)
     nxt = _next_index(ptr)
     vtx = np.stack([cc_id[fcell], fc_id[fidx], fv, fv[nxt]], 1)
@@ -260,14 +272,30 @@ def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
     return xyz, sub_ptr, vtx, sh
 
 
-def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of):
+def _thin_faces(xyz, vtx, sh, L, h, thin):
+    """Fan sub-tets whose face centre lies within thin*h of the line of their face edge."""
+    Lf = 0.0 if L is None else L
+    P = xyz[vtx] + sh * Lf
+    e = P[:, 3] - P[:, 2]
+    u = e / np.linalg.norm(e, axis=1)[:, None]
+    w = P[:, 1] - P[:, 2]
+    dist = np.linalg.norm(w - u * np.einsum("ij,ij->i", w, u)[:, None], axis=1)
+    return np.nonzero(dist < thin * h)[0]
+
+
+def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN):
     exclude: set = set()
+    force: set = set()
+    nxt0 = _next_index(ptr)
+    h = tol / COLLAPSE if tol > 0 else 0.0
     for _ in range(200):
         if tol > 0:
-            new_pos, ptr2, fv2, fs2, keep, merges, members = _collapse(pos, ptr, fv, fs, L, tol, exclude)
+            new_pos, ptr2, fv2, fs2, keep, merges, members, new_id = _collapse(pos, ptr, fv, fs, L, tol, exclude,
+                                                                               force)
         else:
             new_pos, ptr2, fv2, fs2, keep, merges = pos, ptr, fv, fs, np.arange(len(ptr) - 1), 0
             members = [[i] for i in range(len(pos))]
+            new_id = np.arange(len(pos))
         try:
             kc = cells[keep]
             kn = nbrs[keep]
@@ -285,6 +313,28 @@ def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of):
                 raise RuntimeError("cannot build a fold-free fan subgrid")
             exclude |= grow
             continue
+        if tol > 0 and thin > 0:
+            # thin faces: collapse the shortest edge of every face with a thin fan triangle
+            bad = _thin_faces(xyz, vtx, sh, L, h, thin)
+            added = False
+            if len(bad):
+                cnt2 = np.diff(ptr2)
+                fidx2 = np.repeat(np.arange(len(cnt2)), cnt2)
+                nxt2 = _next_index(ptr2)
+                P = new_pos[fv2] + fs2 * (0.0 if L is None else L)
+                elen = np.linalg.norm(P - P[nxt2], axis=1)
+                for f in sorted(set(fidx2[bad].tolist())):
+                    j = ptr2[f] + int(np.argmin(elen[ptr2[f]:ptr2[f + 1]]))
+                    A, B = fv2[j], fv2[nxt2[j]]
+                    of = keep[f]
+                    for e in range(ptr[of], ptr[of + 1]):
+                        if (new_id[fv[e]], new_id[fv[nxt0[e]]]) in ((A, B), (B, A)) and e not in force \
+                                and fv[e] not in exclude and fv[nxt0[e]] not in exclude:
+                            force.add(e)
+                            added = True
+                            break
+            if added:
+                continue
         return xyz, sub_ptr, vtx, sh, merges, len(new_pos), np.bincount(kc, minlength=C)
     raise RuntimeError("edge collapse did not settle")
 
@@ -315,38 +365,48 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
     cells, nbrs, ptr, flat = _original_faces(vor, P, C)
 
     # generators of every Voronoi vertex (points whose region holds it)
-    gens: dict = {}
-    for p in range(len(P)):
-        for v in vor.regions[vor.point_region[p]]:
-            if v >= 0:
-                gens.setdefault(v, []).append(p)
-
-    def canon(members):
-        """Canonical translate of a set of generators: (key, image shift of the frame)."""
-        lab = sorted((int(pid[p]), tuple(int(x) for x in psh[p])) for p in members)
-        ref = lab[0]
-        key = tuple((s, (sh[0] - ref[1][0], sh[1] - ref[1][1], sh[2] - ref[1][2])) for s, sh in lab)
-        return key, np.array(ref[1])
-
+    # generators of every used Voronoi vertex (the points whose region holds it), as codes
+    # pid*125 + (shift+2) in base 5: ordering the codes orders by (seed, image shift)
     used = np.unique(flat)
-    vkey: dict = {}
-    vpos: list = []
-    vid = np.empty(len(used), np.int64)
-    vsh = np.empty((len(used), 3), np.int64)
-    for u, v in enumerate(used):
-        key, rs = canon(gens[int(v)])
-        if key not in vkey:
-            vkey[key] = len(vpos)
-            vpos.append(vor.vertices[v] - rs * L)
-        vid[u] = vkey[key]
-        vsh[u] = rs
+    regs = [vor.regions[vor.point_region[p]] for p in range(len(P))]
+    rv = np.concatenate([np.asarray(r, np.int64) for r in regs])
+    rp = np.repeat(np.arange(len(P)), [len(r) for r in regs])
+    keep = (rv >= 0) & np.isin(rv, used)
+    rv, rp = rv[keep], rp[keep]
+    order = np.lexsort((rp, rv))
+    rv, rp = rv[order], rp[order]
+    w5 = np.array([25, 5, 1])
+    code = pid[rp] * 125 + (psh[rp] + 2) @ w5
+    ngen = np.bincount(np.searchsorted(used, rv), minlength=len(used))
+    gptr = np.concatenate([[0], np.cumsum(ngen)])
+    # reference generator (smallest code) and codes relative to its image
+    ref_code = np.minimum.reduceat(code, gptr[:-1])
+    ref_sh = ((ref_code[:, None] // w5) % 5) - 2
+    rel_sh = psh[rp] - np.repeat(ref_sh, ngen, axis=0)
+    rel = pid[rp] * 125 + (rel_sh + 2) @ w5
+    maxg = int(ngen.max())
+    keys = np.full((len(used), maxg), -1, np.int64)
+    col = np.arange(len(rv)) - np.repeat(gptr[:-1], ngen)
+    keys[np.repeat(np.arange(len(used)), ngen), col] = rel
+    keys = -np.sort(-keys, axis=1)                      # sorted, padding last
+    _, first, vid = np.unique(keys, axis=0, return_index=True, return_inverse=True)
+    vid = vid.ravel()
+    vsh = ref_sh
+    pos = vor.vertices[used[first]] - ref_sh[first] * L
+    # faces keep the order of first appearance of their vertices irrelevant: positions by id
     loc = np.searchsorted(used, flat)
     fv = vid[loc]
     fs = vsh[loc]
-    pos = np.array(vpos)
 
     def face_key_of(a, b):
-        return canon([a, b])
+        """Canonical key rows and frame shifts of the faces between points a and b (arrays)."""
+        ca = pid[a] * 125 + (psh[a] + 2) @ w5
+        cb = pid[b] * 125 + (psh[b] + 2) @ w5
+        r = np.minimum(ca, cb)
+        rs = ((r[:, None] // w5) % 5) - 2
+        ka = pid[a] * 125 + (psh[a] - rs + 2) @ w5
+        kb = pid[b] * 125 + (psh[b] - rs + 2) @ w5
+        return np.stack([np.minimum(ka, kb), np.maximum(ka, kb)], 1), rs
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, L, C,
                                                             collapse * L / n, face_key_of)
@@ -383,7 +443,12 @@ def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
     fs = np.zeros((len(fv), 3), np.int64)
 
     def face_key_of(a, b):
-        return ((min(a, b), max(a, b)) if b < C else (a, -1 - int(b))), np.zeros(3, np.int64)
+        a = np.asarray(a)
+        b = np.asarray(b)
+        inner = b < C
+        k0 = np.where(inner, np.minimum(a, b), a)
+        k1 = np.where(inner, np.maximum(a, b), -1 - b)
+        return np.stack([k0, k1], 1), np.zeros((len(a), 3), np.int64)
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, None, C,
                                                             collapse * h, face_key_of)

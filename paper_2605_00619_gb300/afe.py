@@ -53,6 +53,7 @@ class afe_stats(ctypes.Structure):
         ("nonconverged", ctypes.c_int64),
         ("troubled", ctypes.c_int64),
         ("totals", ctypes.c_double * 5),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
 

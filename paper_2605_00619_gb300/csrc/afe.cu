@@ -52,6 +52,7 @@ struct afe_mesh {
   int diag = 0;
   int pending = 0;  // accumulated status of asynchronous steps
   int profiling = 0;
+  int64_t launches = 0;
   std::vector<cudaEvent_t> ev;  // 5 events per profiled step
   size_t ev_used = 0;
   double t_host = 0;
@@ -173,6 +174,8 @@ afe_status record(afe_mesh* m, int k) {
 }
 
 afe_status enqueue_step(afe_mesh* m, double dt) {
+  // kernels per step: [means + limiter] + (set_dt | cfl + finalize) + predictor + face + corrector + clock
+  m->launches += (m->p.limiter ? 2 : 0) + (dt > 0 ? 1 : 2) + 3 + 1;
   AFE_CUDA(cudaMemsetAsync(m->dm.flags, 0, afe::F_COUNT * sizeof(int), m->stream));
   AFE_TRY(record(m, 0));
   AFE_TRY(enqueue_dt(m, dt));
@@ -538,6 +541,7 @@ afe_status afe_get_stats(const afe_mesh* mc, afe_stats* s) {
   s->picard_max = mx;
   s->nonconverged = flags[afe::F_NONCONV];
   s->troubled = flags[afe::F_TROUBLED];
+  s->kernel_launches = m->launches;
   return AFE_OK;
 }
 
