@@ -177,6 +177,29 @@ afe_status afe_get_diagnostics(const afe_mesh* m, double* qbar, int32_t* iterati
 afe_status afe_set_profiling(afe_mesh* m, int on);
 afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset);
 
+/* Conserved totals of a caller-provided device state, with no device memory allocated by the
+ * call.  The paper has no counterpart: this serves callers that must not call cudaMalloc at
+ * the point of use, e.g. code running inside a framework whose caching allocator owns all
+ * device memory, or a loop that has to stay free of allocation and the implicit device
+ * synchronisation cudaMalloc/cudaFree bring.
+ *   m        handle created earlier (its node weights w_i = M_i 1 are read).
+ *   dq       device array [n_nodes][5] FP64, the state to sum (caller-owned).
+ *   dtotals  device array [5] FP64 receiving sum_i w_i . u_i per conserved variable.
+ *   cuda_stream  stream to run on (NULL = the handle's stream); the call is asynchronous.
+ * The partial sums live in a fixed device array inside the library (AFE_NOALLOC_MAX_PARTIALS
+ * partials of AFE_NOALLOC_CHUNK nodes each, 160 KiB, held by every GPU that loads the library
+ * until the process exits), so meshes with more than AFE_NOALLOC_MAX_NODES nodes are rejected
+ * with AFE_EINVAL.  The first call on a device looks up that array's device address; make
+ * that first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (different streams, no ordering between them) race and must not be
+ * issued.  Nothing in the array needs to start at zero: each call writes every partial it
+ * reads. */
+#define AFE_NOALLOC_CHUNK 65536
+#define AFE_NOALLOC_MAX_PARTIALS 4096
+#define AFE_NOALLOC_MAX_NODES ((int64_t)AFE_NOALLOC_CHUNK * AFE_NOALLOC_MAX_PARTIALS)
+afe_status afe_conserved_totals_noalloc(const afe_mesh* m, const double* dq, double* dtotals,
+                                        void* cuda_stream);
+
 /* Bytes of device memory held by the handle. */
 afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes);
 

@@ -92,6 +92,7 @@ _SIGS = {
     "afe_get_diagnostics": (ctypes.c_int, [_P, _D, _I32, _D, _D]),
     "afe_device_bytes": (ctypes.c_int, [_P, _I64]),
     "afe_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afe_conserved_totals_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "afe_stage_times": (ctypes.c_int, [_P, _D, _I64, ctypes.c_int]),
     "afe_last_error": (ctypes.c_char_p, []),
     "afe_mesh_destroy": (None, [_P]),
@@ -274,6 +275,17 @@ def afe_stage_times(m, reset: bool = True):
     n = ctypes.c_int64()
     _check(lib().afe_stage_times(m, _dptr(ms), ctypes.byref(n), int(bool(reset))))
     return ms, int(n.value)
+
+
+AFE_NOALLOC_CHUNK = 65536
+AFE_NOALLOC_MAX_PARTIALS = 4096
+AFE_NOALLOC_MAX_NODES = AFE_NOALLOC_CHUNK * AFE_NOALLOC_MAX_PARTIALS
+
+
+def afe_conserved_totals_noalloc(m, dq_ptr: int, dtotals_ptr: int, stream: int = 0, check: bool = True) -> int:
+    """Conserved totals of a device state into a device array of 5 doubles, with no device
+    allocation by the call (for callers that may not allocate at the point of use)."""
+    return _check(lib().afe_conserved_totals_noalloc(m, _P(dq_ptr), _P(dtotals_ptr), _P(stream)), check)
 
 
 def afe_mesh_destroy(m):

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -594,3 +595,88 @@ afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------------
+// Conserved totals without device allocation (afe_conserved_totals_noalloc).  The partial
+// sums go to a fixed file-scope device array instead of memory from cudaMalloc.
+
+namespace {
+
+__device__ __align__(256) double g_noalloc_partials[AFE_NOALLOC_MAX_PARTIALS * 5];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// Block b sums w . u over nodes [b*CHUNK, min(n, (b+1)*CHUNK)) in a fixed order.
+__global__ void noalloc_partial_kernel(const double* __restrict__ w, const double* __restrict__ u, int64_t n,
+                                       double* partials) {
+  __shared__ double sh[5][256];
+  const int64_t a = (int64_t)blockIdx.x * AFE_NOALLOC_CHUNK;
+  const int64_t b = min(n, a + (int64_t)AFE_NOALLOC_CHUNK);
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += wi * u[i * 5 + v];
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) sh[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void noalloc_final_kernel(const double* partials, int np, double* out) {
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int b = 0; b < np; ++b) s += partials[b * 5 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+extern "C" afe_status afe_conserved_totals_noalloc(const afe_mesh* m, const double* dq, double* dtotals,
+                                                   void* cuda_stream) {
+  if (!m || !dq || !dtotals) return fail(AFE_EINVAL, "NULL argument");
+  const int64_t n = m->topo.n_nodes;
+  if (n > AFE_NOALLOC_MAX_NODES)
+    return fail(AFE_EINVAL, "afe_conserved_totals_noalloc: " + std::to_string(n) +
+                                " nodes exceed the fixed scratch limit of " + std::to_string(AFE_NOALLOC_MAX_NODES) +
+                                " nodes (" + std::to_string(AFE_NOALLOC_MAX_PARTIALS) + " partials of " +
+                                std::to_string(AFE_NOALLOC_CHUNK) + ")");
+  if (m->device < 0 || m->device >= kNoallocMaxDevices) return fail(AFE_EINVAL, "device index out of range");
+  int prev = -1;
+  AFE_CUDA(cudaGetDevice(&prev));
+  if (prev != m->device) AFE_CUDA(cudaSetDevice(m->device));
+  double* scratch = nullptr;
+  {
+    // one-time set-up per device, with that device current: the host-side symbol is only a
+    // stand-in, the kernels need the array's device address
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[m->device]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+      if (e != cudaSuccess) {
+        if (prev != m->device) cudaSetDevice(prev);
+        return fail(AFE_ECUDA, std::string("cudaGetSymbolAddress(g_noalloc_partials): ") + cudaGetErrorString(e));
+      }
+      g_noalloc_ptr[m->device] = (double*)p;
+    }
+    scratch = g_noalloc_ptr[m->device];
+  }
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : m->stream;
+  const int np = (int)((n + AFE_NOALLOC_CHUNK - 1) / AFE_NOALLOC_CHUNK);
+  noalloc_partial_kernel<<<np, 256, 0, st>>>(m->dm.wvec, dq, n, scratch);
+  noalloc_final_kernel<<<1, 32, 0, st>>>(scratch, np, dtotals);
+  cudaError_t e = cudaGetLastError();
+  if (prev != m->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return fail(AFE_ECUDA, std::string("afe_conserved_totals_noalloc launch: ") + cudaGetErrorString(e));
+  return AFE_OK;
+}
