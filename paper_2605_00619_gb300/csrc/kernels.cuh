@@ -16,13 +16,14 @@
 #include <cstdint>
 
 #include "refelem.hpp"
+#include "topology.hpp"
 
 namespace afe {
 
 constexpr int np_of(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
 constexpr int nf_of(int N) { return (N + 1) * (N + 2) / 2; }
 
-enum FlagIndex { F_NONCONV = 0, F_NONFINITE = 1, F_TROUBLED = 2, F_ITERSUM = 3, F_COUNT = 8 };
+enum FlagIndex { F_NONCONV = 0, F_NONFINITE = 1, F_TROUBLED = 2, F_ITERSUM = 3, F_TIMEOUT = 4, F_COUNT = 8 };
 
 struct DevMesh {
   int N;
@@ -34,6 +35,7 @@ struct DevMesh {
   const int64_t* minv_ptr;
   const uint16_t* A;
   const double* geo;
+  float* geo32;  // FP32 copy of geo ([T][12]), reduced-precision path only
   const int64_t* inc_ptr;
   const uint32_t* inc;
   const int32_t* slot_cell;
@@ -152,20 +154,21 @@ __global__ void assemble_mass_kernel(DevMesh m, const RefData* __restrict__ ref)
     const int64_t n0 = m.node_ptr[c];
     const int Ni = (int)(m.node_ptr[c + 1] - n0);
     double* M = m.minv64 + m.minv_ptr[c];
-    for (int64_t e = threadIdx.x; e < (int64_t)Ni * Ni; e += blockDim.x) M[e] = 0.0;
+    const int LD = minv_ld(Ni);
+    for (int64_t e = threadIdx.x; e < m.minv_ptr[c + 1] - m.minv_ptr[c]; e += blockDim.x) M[e] = 0.0;
     __syncthreads();
     for (int64_t k = m.sub_ptr[c]; k < m.sub_ptr[c + 1]; ++k) {
       const double det = m.geo[k * 10 + 9];
       const uint16_t* Ak = m.A + k * Np;
       for (int e = threadIdx.x; e < Np * Np; e += blockDim.x) {
         const int j = e / Np, l = e % Np;
-        M[(int64_t)Ak[j] * Ni + Ak[l]] += det * ref->M[j][l];
+        M[(int64_t)Ak[j] * LD + Ak[l]] += det * ref->M[j][l];
       }
       __syncthreads();
     }
     for (int n = threadIdx.x; n < Ni; n += blockDim.x) {
       double s = 0.0;
-      for (int l = 0; l < Ni; ++l) s += M[(int64_t)n * Ni + l];
+      for (int l = 0; l < Ni; ++l) s += M[(int64_t)n * LD + l];
       m.wvec[n0 + n] = s;
     }
     __syncthreads();
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(256) invert_spd_kernel(DevMesh m) {
   const int tid = threadIdx.x;
   for (int64_t c = blockIdx.x; c < m.C; c += gridDim.x) {
     const int n = (int)(m.node_ptr[c + 1] - m.node_ptr[c]);
+    const int LD = minv_ld(n);
     double* A = m.minv64 + m.minv_ptr[c];
     const int T = (n + B - 1) / B;
     auto load = [&](double (*dst)[B + 1], int ib, int jb, bool ident) {
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(256) invert_spd_kernel(DevMesh m) {
         const int r = e / B, q = e % B;
         const int gr = ib * B + r, gq = jb * B + q;
         double v = (ident && r == q) ? 1.0 : 0.0;
-        if (gr < n && gq < n) v = A[(int64_t)gr * n + gq];
+        if (gr < n && gq < n) v = A[(int64_t)gr * LD + gq];
         dst[r][q] = v;
       }
     };
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(256) invert_spd_kernel(DevMesh m) {
       for (int e = tid; e < B * B; e += blockDim.x) {
         const int r = e / B, q = e % B;
         const int gr = ib * B + r, gq = jb * B + q;
-        if (gr < n && gq < n) A[(int64_t)gr * n + gq] = src[r][q];
+        if (gr < n && gq < n) A[(int64_t)gr * LD + gq] = src[r][q];
       }
     };
     for (int kb = 0; kb < T; ++kb) {
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(256) invert_spd_kernel(DevMesh m) {
               double s = 0.0;
 #pragma unroll 8
               for (int k = 0; k < B; ++k) s += sY[r][k] * sX[k][q];
-              A[(int64_t)gr * n + gq] -= s;
+              A[(int64_t)gr * LD + gq] -= s;
             }
           }
           __syncthreads();
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(256) invert_spd_kernel(DevMesh m) {
             double s = 0.0;
 #pragma unroll 8
             for (int k = 0; k < B; ++k) s += sY[r][k] * sD[k][q];
-            A[(int64_t)gr * n + gq] = -s;
+            A[(int64_t)gr * LD + gq] = -s;
           }
         }
         __syncthreads();
@@ -297,17 +301,18 @@ __global__ void __launch_bounds__(256) invert_spd_kernel(DevMesh m) {
 __global__ void symmetrize_kernel(DevMesh m, int make32) {
   for (int64_t c = blockIdx.x; c < m.C; c += gridDim.x) {
     const int n = (int)(m.node_ptr[c + 1] - m.node_ptr[c]);
+    const int LD = minv_ld(n);
     double* A = m.minv64 + m.minv_ptr[c];
     for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
       const int r = (int)(e / n), q = (int)(e % n);
       if (q < r) continue;
-      const double v = 0.5 * (A[(int64_t)r * n + q] + A[(int64_t)q * n + r]);
-      A[(int64_t)r * n + q] = v;
-      A[(int64_t)q * n + r] = v;
+      const double v = 0.5 * (A[(int64_t)r * LD + q] + A[(int64_t)q * LD + r]);
+      A[(int64_t)r * LD + q] = v;
+      A[(int64_t)q * LD + r] = v;
     }
     __syncthreads();
     if (make32)
-      for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x)
+      for (int64_t e = threadIdx.x; e < m.minv_ptr[c + 1] - m.minv_ptr[c]; e += blockDim.x)
         m.minv32[m.minv_ptr[c] + e] = (float)A[e];
     __syncthreads();
   }
@@ -564,8 +569,9 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
         Real acc[NT * 5];
 #pragma unroll
         for (int c2 = 0; c2 < NT * 5; ++c2) acc[c2] = 0;
+        const int LD = minv_ld(Ni);
         for (int l = 0; l < Ni; ++l) {
-          const Real a = minv[(int64_t)l * Ni + n];
+          const Real a = minv[(int64_t)l * LD + n];
           const Real* r = RHS + l * NT * 5;
 #pragma unroll
           for (int c2 = 0; c2 < NT * 5; ++c2) acc[c2] += a * r[c2];
@@ -839,8 +845,9 @@ __global__ void __launch_bounds__(256) corrector_kernel(DevMesh m, const RefData
     double wdu[5] = {0, 0, 0, 0, 0};
     for (int n = tid; n < Ni; n += blockDim.x) {
       Real acc[5] = {0, 0, 0, 0, 0};
+      const int LD = minv_ld(Ni);
       for (int l = 0; l < Ni; ++l) {
-        const Real a = minv[(int64_t)l * Ni + n];
+        const Real a = minv[(int64_t)l * LD + n];
 #pragma unroll
         for (int v = 0; v < 5; ++v) acc[v] += a * r[l * 5 + v];
       }

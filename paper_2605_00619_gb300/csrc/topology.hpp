@@ -12,6 +12,10 @@
 
 namespace afe {
 
+// Leading dimension of a cell's M_i^-1 block: N_i rounded up to a multiple of 4, so that
+// every row starts on a 16-byte boundary (bulk copies of whole rows).
+inline constexpr int minv_ld(int n) { return (n + 3) & ~3; }
+
 struct Topology {
   int N = 0, Np = 0, Nt = 0, Nf = 0;
   int64_t C = 0, T = 0, n_nodes = 0, n_slots = 0, n_groups = 0;
@@ -20,7 +24,7 @@ struct Topology {
   std::vector<int64_t> node_ptr;   // [C+1] global node offset of each cell
   std::vector<int64_t> sub_ptr;    // [C+1] sub-tet offset of each cell
   std::vector<int64_t> slot_ptr;   // [C+1] face-slot offset of each cell
-  std::vector<int64_t> minv_ptr;   // [C+1] offset of the dense N_i x N_i block of each cell
+  std::vector<int64_t> minv_ptr;   // [C+1] offset of the dense N_i x minv_ld(N_i) block of each cell
 
   std::vector<uint16_t> A;         // [T*Np] cell-local node of sub-tet node j
   std::vector<double> geo;         // [T*10] adj(J) row-major (adj = det(J) J^-1), det(J)
