@@ -48,7 +48,7 @@ struct afe_mesh {
   void* scratch = nullptr;
   int64_t scratch_stride = 0;
   int pred_grid = 0;
-  int f32_rows = 0;      // M_i^-1 rows per pipeline stage of the FP32 predictor (0: not used)
+  int f32_ok = 0;        // the shared-memory FP32 predictor is used
   size_t f32_smem = 0;
   double* d_totals_partial = nullptr;
   double* d_totals = nullptr;
@@ -98,17 +98,16 @@ namespace {
 
 template <int N, typename Real>
 void launch_predictor(afe_mesh* m) {
-  if (sizeof(Real) == 4 && m->f32_rows > 0) {
-    afe::predictor_f32_kernel<N><<<m->n_sm, afe::kF32Threads, m->f32_smem, m->stream>>>(m->dm, m->d_ref, m->f32_rows,
-                                                                                        m->diag);
+  if (sizeof(Real) == 4 && m->f32_ok) {
+    afe::predictor_f32_kernel<N><<<m->n_sm, afe::kF32Threads, m->f32_smem, m->stream>>>(m->dm, m->d_ref, m->diag,
+                                                                                        (int)m->f32_smem);
     return;
   }
   afe::predictor_kernel<N, Real><<<m->pred_grid, 256, 0, m->stream>>>(m->dm, m->d_ref, (Real*)m->scratch,
                                                                       m->scratch_stride, m->diag);
 }
 
-// Shared-memory plan of the FP32 predictor: the largest M_i^-1 stage (rows per stage) that
-// fits next to the cell's working set; 0 if the cells are too large (global-scratch kernel).
+// Shared-memory plan of the FP32 predictor; cells too large for it use the global-scratch kernel.
 template <int N>
 afe_status plan_f32(afe_mesh* m) {
   cudaFuncAttributes fa;
@@ -116,16 +115,15 @@ afe_status plan_f32(afe_mesh* m) {
   int optin = 0;
   AFE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
   const size_t limit = (size_t)optin - fa.sharedSizeBytes - 1024;
-  m->f32_rows = 0;
-  for (int rows : {16, 8, 4, 2, 1}) {
-    const size_t b = afe::predictor_f32_smem(N, m->dm.Nmax, rows);
-    if (b <= limit) {
-      m->f32_rows = rows;
-      m->f32_smem = b;
-      AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-      break;
-    }
-  }
+  m->f32_ok = 0;
+  if (m->dm.Nmax > afe::predictor_f32_max_nodes(N)) return AFE_OK;
+  const size_t need = afe::predictor_f32_smem(N, m->dm.Nmax, m->dm.Smax);
+  if (need > limit) return AFE_OK;
+  // all the shared memory the block may have: smaller cells get a deeper M_i^-1 ring
+  const size_t b = limit / 128 * 128;
+  m->f32_ok = 1;
+  m->f32_smem = b;
+  AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
   return AFE_OK;
 }
 
@@ -391,12 +389,23 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
     AFE_CUDA(cudaMemcpy(d.mu, mu0.data(), T.C * sizeof(double), cudaMemcpyHostToDevice));
   }
   if (p->precision == AFE_FP32) {
-    AFE_TRY(M->alloc(&d.geo32, (size_t)T.T * 12));
-    afe::geo32_kernel<<<(int)((T.T + 255) / 256), 256, 0, M->stream>>>(d, T.T);
+    const int blocks = (int)((T.T + 255) / 256);
     switch (p->order) {
-      case 1: AFE_TRY(plan_f32<1>(M)); break;
-      case 2: AFE_TRY(plan_f32<2>(M)); break;
-      default: AFE_TRY(plan_f32<3>(M)); break;
+      case 1:
+        AFE_TRY(M->alloc(&d.sub32, (size_t)T.T * afe::f32_rec_bytes(1)));
+        afe::sub32_kernel<1><<<blocks, 256, 0, M->stream>>>(d, T.T);
+        AFE_TRY(plan_f32<1>(M));
+        break;
+      case 2:
+        AFE_TRY(M->alloc(&d.sub32, (size_t)T.T * afe::f32_rec_bytes(2)));
+        afe::sub32_kernel<2><<<blocks, 256, 0, M->stream>>>(d, T.T);
+        AFE_TRY(plan_f32<2>(M));
+        break;
+      default:
+        AFE_TRY(M->alloc(&d.sub32, (size_t)T.T * afe::f32_rec_bytes(3)));
+        afe::sub32_kernel<3><<<blocks, 256, 0, M->stream>>>(d, T.T);
+        AFE_TRY(plan_f32<3>(M));
+        break;
     }
   }
   // predictor scratch (persistent grid, one slice per block)
@@ -404,7 +413,7 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
     const int64_t per = (int64_t)T.Nmax * T.Nt * 5 * 3 + (int64_t)T.Smax * T.Nt * T.Np * 5 * 4;
     M->scratch_stride = (per + 31) / 32 * 32;
     M->pred_grid = (int)std::min<int64_t>(T.C, (int64_t)M->n_sm * 2);
-    if (!(p->precision == AFE_FP32 && M->f32_rows > 0)) {  // the shared-memory FP32 kernel needs none
+    if (!(p->precision == AFE_FP32 && M->f32_ok)) {  // the shared-memory FP32 kernel needs none
       void* s;
       AFE_TRY(M->alloc((char**)&s, (size_t)M->scratch_stride * M->pred_grid * rb));
       M->scratch = s;

@@ -35,7 +35,7 @@ struct DevMesh {
   const int64_t* minv_ptr;
   const uint16_t* A;
   const double* geo;
-  float* geo32;  // FP32 copy of geo ([T][12]), reduced-precision path only
+  unsigned char* sub32;  // packed FP32 sub-tet records, reduced-precision path only
   const int64_t* inc_ptr;
   const uint32_t* inc;
   const int32_t* slot_cell;

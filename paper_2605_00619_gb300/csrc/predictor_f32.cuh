@@ -2,25 +2,28 @@
 //
 // One block of 512 threads per cell (persistent: blocks take cells from a work counter).
 // The cell's working set stays in shared memory for the whole fixed-point iteration:
-//   sq   [N_i][Nt*5]  space-time nodal coefficients q (node-major)
-//   srhs [N_i][Nt*5]  right-hand side sum_k A_k^T R_k (zeroed and gathered every iteration)
+//   sq   [N_i][Nt*5|1]  space-time nodal coefficients q (node-major, odd row stride)
+//   srhs [N_i][Nt*5|1]  right-hand side sum_k A_k^T R_k, then Y, then the volume term
 //   sR   [CH][Nt][Np][5]  per-chunk sub-tet results R_{k,t} (deterministic gather buffer)
 //   sB   [warps][3][Np][5]  per-warp flux pre-contraction of one (sub-tet, time)
 //   sM   [NSTAGE][rows][LD] pipelined stages of M_i^-1
 // Per iteration:
 //   1. for chunks of CH sub-tets: every warp takes (sub-tet k, time t) pairs; lanes j < Np
 //      evaluate the flux at node j and pre-contract it with dt adj(J_k) (f*, g*, h*); lanes
-//      m < Np then form R[m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v]; after the chunk each
-//      thread adds, for the nodes it owns, the chunk's incidences in (k, j) order (fixed
-//      order: the sum is bitwise reproducible and has no atomics);
+//      (m, v) then form R[m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v] in 4-row tiles; after
+//      the chunk each thread adds, in registers for the nodes it owns, the chunk's incidences
+//      in (k, j) order (fixed order: the sum is bitwise reproducible and has no atomics);
 //   2. Y = M_i^-1 RHS with M_i^-1 streamed through shared memory in stages of `rows` rows by
-//      cp.async.bulk (TMA bulk copies, completion on an mbarrier), each thread owning up to two
-//      rows of Y (M_i^-1 is symmetric: row l of the stage serves column l);
+//      cp.async.bulk (TMA bulk copies, completion on an mbarrier); thread (row group, time
+//      slice) keeps 4 x 5 tiles of Y in registers (M_i^-1 is symmetric: row l of the stage
+//      serves column l);
 //      q^{r+1}[n,s] = u^[n] - sum_t K1t^-1[s,t] Y[n,t] and the residual, in registers.
 // Epilogue: vol = sum_k A_k^T sum_d S^_d^T adj(J_k) F_bar_k, and q_bar, F_bar . n on the face
 // slots, as the FP64 kernel.  Every mbarrier wait is bounded; a wait that runs out sets
 // flags[F_TIMEOUT], drains the copies in flight (bounded again) and the block returns.
 #pragma once
+
+#include <algorithm>
 
 #include "kernels.cuh"
 
@@ -28,8 +31,10 @@ namespace afe {
 
 constexpr int kF32Threads = 512;
 constexpr int kF32Warps = kF32Threads / 32;
-constexpr int kF32Chunk = 8;     // sub-tets per gather chunk
-constexpr int kF32Stages = 3;    // M_i^-1 pipeline depth
+constexpr int kF32Chunk = 16;    // sub-tets per gather chunk
+constexpr int kF32Rows = 16;     // rows of M_i^-1 per pipeline stage
+constexpr int kF32MaxStages = 8;
+constexpr int kF32Consumers = kF32Warps - 1;  // warps that apply M_i^-1 (the last one loads it)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -41,6 +46,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -71,17 +80,37 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Bytes of dynamic shared memory the FP32 predictor needs for a mesh.
-inline size_t predictor_f32_smem(int N, int Nmax, int rows) {
-  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, NC = (N + 1) * 5;
+// Largest cell (nodes) the FP32 predictor handles: up to kF32Items (node, time slice) gather
+// items and two 4-row groups of the M_i^-1 apply per thread.
+constexpr int kF32MaxNodes = 640;
+constexpr int kF32Items = 5;  // ceil(640 * 4 / 512)
+inline int predictor_f32_max_nodes(int N) {
+  const int by_items = kF32Items * kF32Threads / (N + 1);
+  const int by_rows = 8 * (kF32Consumers * 32 / (N + 1));
+  return std::min(kF32MaxNodes, std::min(by_items, by_rows));
+}
+
+// Row stride (floats) of the per-node arrays in shared memory: Nt*5 made odd, so that one
+// thread per row touches 32 different banks.
+constexpr int f32_row_stride(int N) { return ((N + 1) * 5) | 1; }
+
+// Packed FP32 sub-tet record: adj(J) row-major (9 floats), det J, then the Np cell-local node
+// ids (uint16); padded to 16 bytes so that a cell's records are one bulk copy.
+constexpr int f32_rec_bytes(int N) { return (40 + 2 * np_of(N) + 15) / 16 * 16; }
+
+// Dynamic shared memory of the FP32 predictor: a fixed part (chunk results, per-warp staging,
+// sub-tet records) and, per cell, q and RHS rows followed by a ring of M_i^-1 stages that
+// takes whatever is left.  Returns the bytes needed for the largest cell with one stage.
+inline size_t f32_fixed_smem(int N, int Smax) {
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   auto up = [](size_t x) { return (x + 127) / 128 * 128; };
-  size_t b = 0;
-  b += up((size_t)Nmax * NC * 4);                                 // sq
-  b += up((size_t)Nmax * NC * 4);                                 // srhs
-  b += up((size_t)kF32Stages * rows * minv_ld(Nmax) * 4);         // sM
-  b += up((size_t)kF32Chunk * (N + 1) * Np * 5 * 4);              // sR
-  b += up((size_t)kF32Warps * 3 * Np * 5 * 4);                    // sB
-  return b;
+  return up((size_t)kF32Chunk * (N + 1) * Np * 5 * 4) + up((size_t)kF32Warps * 3 * Np * 5 * 4) +
+         up((size_t)Smax * ((40 + 2 * Np + 15) / 16 * 16));
+}
+inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
+  auto up = [](size_t x) { return (x + 127) / 128 * 128; };
+  return f32_fixed_smem(N, Smax) + 2 * up((size_t)Nmax * f32_row_stride(N) * 4) +
+         (size_t)kF32Rows * minv_ld(Nmax) * 4;
 }
 
 // flux pre-contraction at one (sub-tet, time, local node j): out[d][v] = sum_e G[d][e] F_e[v]
@@ -91,9 +120,9 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
                                                   const float* __restrict__ g, int j, int t, bool visc, float mu,
                                                   float kap, float gam, float Rg, float scale,
                                                   const float (*sD)[np_of(N)][np_of(N)], float out[3][5]) {
-  constexpr int NP = np_of(N), NC = (N + 1) * 5;
+  constexpr int NP = np_of(N), SQ = f32_row_stride(N);
   float Q[5];
-  const float* qn = sq + Ak[j] * NC + t * 5;
+  const float* qn = sq + Ak[j] * SQ + t * 5;
 #pragma unroll
   for (int v = 0; v < 5; ++v) Q[v] = qn[v];
   float gq[3][5];
@@ -104,7 +133,7 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
 #pragma unroll
       for (int v = 0; v < 5; ++v) gx[d][v] = 0.f;
     for (int l = 0; l < NP; ++l) {
-      const float* ql = sq + Ak[l] * NC + t * 5;
+      const float* ql = sq + Ak[l] * SQ + t * 5;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const float dd = sD[d][j][l];
@@ -128,52 +157,66 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
 
 template <int N>
 __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m, const RefData* __restrict__ ref,
-                                                                        int rows, int diag) {
-  constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), NC = NT * 5;
+                                                                        int diag, int smem_bytes) {
+  constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), NC = NT * 5, SR = f32_row_stride(N);
+  constexpr int NPP = (NP + 3) / 4 * 4;  // rows of sSt padded to 16 bytes
+  constexpr int RG = kF32Threads / NT;   // 4-row groups per pass of the M_i^-1 apply
+  constexpr int REC = f32_rec_bytes(N);  // bytes per sub-tet record
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ float sSt[3][NP][NP];   // sSt[d][j][m] = S^_d[m][j]  (iteration contraction, lane = m)
+  __shared__ __align__(16) float sSt[3][NP][NPP];  // sSt[d][j][m] = S^_d[m][j] (zero padded)
   __shared__ float sSo[3][NP][NP];   // sSo[d][j][m] = S^_d[j][m]  (volume term, lane = m)
   __shared__ float sD[3][NP][NP];    // nodal derivative matrices (viscous fluxes)
   __shared__ float sK[NT][NT];
   __shared__ float sW[NT];
-  __shared__ __align__(8) uint64_t sbar[kF32Stages];
+  __shared__ __align__(8) uint64_t sbar;
+  __shared__ __align__(8) uint64_t sfull[kF32MaxStages];
+  __shared__ __align__(8) uint64_t sempty[kF32MaxStages];
+  __shared__ int sAbort;
   __shared__ float sred[2][kF32Warps];
   __shared__ int64_t sCell;
-  __shared__ int sAbort;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Nmax = m.Nmax;
-  const int LDmax = minv_ld(Nmax);
   auto up = [](size_t x) { return (x + 127) / 128 * 128; };
   unsigned char* p = smem_raw;
-  float* sq = (float*)p;
-  p += up((size_t)Nmax * NC * 4);
-  float* srhs = (float*)p;
-  p += up((size_t)Nmax * NC * 4);
-  float* sM = (float*)p;
-  p += up((size_t)kF32Stages * rows * LDmax * 4);
-  float* sR = (float*)p;
+  float* sR = (float*)p;    // [CH][NT][NP][5]
   p += up((size_t)kF32Chunk * NT * NP * 5 * 4);
-  float* sB = (float*)p + warp * 3 * NP * 5;
+  float* sBw = (float*)p;   // [warps][3][NP][5]
+  p += up((size_t)kF32Warps * 3 * NP * 5 * 4);
+  unsigned char* srec = p;  // [S][REC] sub-tet records of the current cell
+  p += up((size_t)m.Smax * REC);
+  unsigned char* const cell_base = p;  // per cell: sq [Ni][SR], srhs [Ni][SR], M_i^-1 ring
+  float* sB = sBw + warp * 3 * NP * 5;
+  (void)Nmax;
 
+  for (int e = tid; e < 3 * NP * NPP; e += kF32Threads) {
+    const int d = e / (NP * NPP), j = (e / NPP) % NP, mm = e % NPP;
+    sSt[d][j][mm] = mm < NP ? (float)ref->S[d][mm][j] : 0.f;
+  }
   for (int e = tid; e < 3 * NP * NP; e += kF32Threads) {
     const int d = e / (NP * NP), r = (e / NP) % NP, c = e % NP;
-    sSt[d][c][r] = (float)ref->S[d][r][c];
     sSo[d][r][c] = (float)ref->S[d][r][c];
     sD[d][r][c] = (float)ref->D[d][r][c];
   }
   if (tid < NT * NT) sK[tid / NT][tid % NT] = (float)ref->K1tinv[tid / NT][tid % NT];
   if (tid < NT) sW[tid] = (float)ref->w[tid];
   if (tid == 0) {
-    for (int s = 0; s < kF32Stages; ++s) mbar_init(&sbar[s], 1);
+    mbar_init(&sbar, 1);
+    for (int i = 0; i < kF32MaxStages; ++i) {
+      mbar_init(&sfull[i], 1);
+      mbar_init(&sempty[i], kF32Consumers);
+    }
     sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  uint32_t phase = 0;  // bit s: parity of the next completion of stage s (same in every thread)
+  uint32_t phase = 0;
+  uint32_t fpar = 0, epar = 0;  // parities of the next completion of sfull[s] / sempty[s]
   const float dt = (float)*m.dt;
   const float gam = (float)m.gamma, Rg = (float)m.Rgas;
   const float tol = (float)m.tol;
+  auto rec_g = [&](int k) { return reinterpret_cast<const float*>(srec + (size_t)k * REC); };
+  auto rec_a = [&](int k) { return reinterpret_cast<const uint16_t*>(srec + (size_t)k * REC + 40); };
 
   for (;;) {
     if (tid == 0) sCell = atomicAdd(m.work, 1);
@@ -189,61 +232,87 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
     const float kap = (float)cell_kappa(m, m.mu[c]);
     const bool visc = (mu != 0.f) || (kap != 0.f);
     const float* minv = m.minv32 + m.minv_ptr[c];
-    const int nblk = (Ni + rows - 1) / rows;
+    const uint32_t* inc = m.inc + m.inc_ptr[n0];
+    float* sq = reinterpret_cast<float*>(cell_base);
+    float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
+    float* ring = reinterpret_cast<float*>(cell_base + 2 * up((size_t)Ni * SR * 4));
+    const int stage_floats = kF32Rows * LD;
+    const int nstage = min(kF32MaxStages,
+                           (int)(((size_t)smem_bytes - (size_t)(reinterpret_cast<unsigned char*>(ring) - smem_raw)) /
+                                 ((size_t)stage_floats * 4)));
+    const int nblk = (Ni + kF32Rows - 1) / kF32Rows;
 
-    // rows owned by this thread (n = tid, tid + 512) and their u^ in registers
+    // the cell's sub-tet records arrive by one bulk copy while the state is loaded
+    if (tid == 0) {
+      mbar_expect_tx(&sbar, (uint32_t)(S * REC));
+      bulk_g2s(srec, m.sub32 + (size_t)kbase * REC, (uint32_t)(S * REC), &sbar);
+    }
     float uh[2][5];
-    int cur[2], cend[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int n = tid + r * kF32Threads;
-      cur[r] = cend[r] = 0;
       if (n < Ni) {
         const double* un = m.u + (n0 + n) * 5;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           uh[r][v] = (float)un[v];
 #pragma unroll
-          for (int t = 0; t < NT; ++t) sq[n * NC + t * 5 + v] = uh[r][v];
+          for (int t = 0; t < NT; ++t) sq[n * SR + t * 5 + v] = uh[r][v];
         }
       } else {
 #pragma unroll
         for (int v = 0; v < 5; ++v) uh[r][v] = 0.f;
       }
     }
+    if (tid == 0 && !mbar_wait_bounded(&sbar, phase & 1u)) {
+      atomicOr(&m.flags[F_TIMEOUT], 1);
+      sAbort = 1;
+    }
     __syncthreads();
+    if (sAbort) {
+      // a bulk copy that never completed: wait once more (bounded) for it, then leave
+      if (tid == 0) (void)mbar_wait_bounded(&sbar, phase & 1u);
+      return;
+    }
+    (void)mbar_wait_bounded(&sbar, phase & 1u);  // completed: returns at once
+    phase ^= 1u;
+    __syncthreads();
+
+    // gather items of this thread: (node, time slice) = (i / NT, i % NT), i = tid + 512 r
+    int inode[kF32Items], cur[kF32Items], cend[kF32Items];
+#pragma unroll
+    for (int r = 0; r < kF32Items; ++r) {
+      const int i = tid + r * kF32Threads;
+      inode[r] = i < Ni * NT ? i / NT : -1;
+      cur[r] = cend[r] = 0;
+    }
+    constexpr int RGC = kF32Consumers * 32 / NT;  // 4-row groups per pass of the consumers
+    const int tt = tid % NT, rg0 = tid / NT;
+    const bool consumer = warp < kF32Consumers;
+    const bool act0 = consumer && rg0 < RGC && 4 * rg0 < Ni;
+    const bool act1 = consumer && rg0 < RGC && 4 * (rg0 + RGC) < Ni;
 
     int it = 0;
     bool conv = false;
     while (!conv && it < m.picard_max) {
       ++it;
-      // prefetch the first stages of M_i^-1 while the right-hand side is formed
-      if (tid == 0) {
-        for (int b = 0; b < kF32Stages && b < nblk; ++b) {
-          const int rb = min(rows, Ni - b * rows);
-          mbar_expect_tx(&sbar[b], (uint32_t)(rb * LD * 4));
-          bulk_g2s(sM + (size_t)b * rows * LDmax, minv + (size_t)b * rows * LD, (uint32_t)(rb * LD * 4), &sbar[b]);
+      // ---- 1. right-hand side RHS[n][t] = sum over incidences (k, j) of R_{k,t}[j]
+      float racc[kF32Items][5];
+#pragma unroll
+      for (int r = 0; r < kF32Items; ++r) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) racc[r][v] = 0.f;
+        if (inode[r] >= 0) {
+          cur[r] = (int)(m.inc_ptr[n0 + inode[r]] - m.inc_ptr[n0]);
+          cend[r] = (int)(m.inc_ptr[n0 + inode[r] + 1] - m.inc_ptr[n0]);
         }
       }
-      // ---- 1. right-hand side
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int n = tid + r * kF32Threads;
-        if (n < Ni) {
-#pragma unroll
-          for (int e = 0; e < NC; ++e) srhs[n * NC + e] = 0.f;
-          cur[r] = (int)(m.inc_ptr[n0 + n] - m.inc_ptr[n0]);
-          cend[r] = (int)(m.inc_ptr[n0 + n + 1] - m.inc_ptr[n0]);
-        }
-      }
-      const uint32_t* inc = m.inc + m.inc_ptr[n0];
       for (int kc = 0; kc < S; kc += kF32Chunk) {
         const int nk = min(kF32Chunk, S - kc);
         for (int pr = warp; pr < nk * NT; pr += kF32Warps) {
           const int kl = pr / NT, t = pr % NT;
-          const int64_t kg = kbase + kc + kl;
-          const uint16_t* Ak = m.A + kg * NP;
-          const float* g = m.geo32 + kg * 12;
+          const float* g = rec_g(kc + kl);
+          const uint16_t* Ak = rec_a(kc + kl);
           if (lane < NP) {
             float out[3][5];
             f32_flux_contract<N>(sq, Ak, g, lane, t, visc, mu, kap, gam, Rg, dt, sD, out);
@@ -253,96 +322,195 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
               for (int v = 0; v < 5; ++v) sB[(d * NP + lane) * 5 + v] = out[d][v];
           }
           __syncwarp();
-          if (lane < NP) {
-            float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+          // R[m][v] = w_t sum_d sum_j S^_d[m][j] B[d][j][v]: lane (mg, v) forms rows 4mg..4mg+3
+          if (lane < (NPP / 4) * 5) {
+            const int mg = lane / 5, v = lane % 5;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
-#pragma unroll 4
+#pragma unroll 5
               for (int j = 0; j < NP; ++j) {
-                const float s = sSt[d][j][lane];
-                const float* b = sB + (d * NP + j) * 5;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) acc[v] += s * b[v];
+                const float4 s4 = *reinterpret_cast<const float4*>(&sSt[d][j][4 * mg]);
+                const float b = sB[(d * NP + j) * 5 + v];
+                acc.x += s4.x * b;
+                acc.y += s4.y * b;
+                acc.z += s4.z * b;
+                acc.w += s4.w * b;
               }
-            float* dst = sR + ((kl * NT + t) * NP + lane) * 5;
+            float* dst = sR + ((kl * NT + t) * NP + 4 * mg) * 5 + v;
+            const float wt = sW[t];
+            const float av[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
-            for (int v = 0; v < 5; ++v) dst[v] = sW[t] * acc[v];
+            for (int i = 0; i < 4; ++i)
+              if (4 * mg + i < NP) dst[5 * i] = wt * av[i];
           }
           __syncwarp();
         }
         __syncthreads();
-        // gather this chunk's incidences, in (k, j) order, into the owned rows
+        // gather this chunk's incidences, in (k, j) order, into the items' registers
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int n = tid + r * kF32Threads;
-          if (n >= Ni) continue;
+        for (int r = 0; r < kF32Items; ++r) {
+          if (inode[r] < 0) continue;
+          const int t = (tid + r * kF32Threads) % NT;
           while (cur[r] < cend[r]) {
             const uint32_t w = inc[cur[r]];
             const int k = (int)(w >> 5) - kc;
             if (k >= nk) break;
-            const int j = (int)(w & 31);
+            const float* src = sR + ((k * NT + t) * NP + (int)(w & 31)) * 5;
 #pragma unroll
-            for (int t = 0; t < NT; ++t)
-#pragma unroll
-              for (int v = 0; v < 5; ++v) srhs[n * NC + t * 5 + v] += sR[((k * NT + t) * NP + j) * 5 + v];
+            for (int v = 0; v < 5; ++v) racc[r][v] += src[v];
             ++cur[r];
           }
         }
         __syncthreads();
       }
-      // ---- 2. Y = M_i^-1 RHS (streamed), update and residual
-      float acc[2][NC];
+#pragma unroll
+      for (int r = 0; r < kF32Items; ++r) {
+        if (inode[r] < 0) continue;
+        const int t = (tid + r * kF32Threads) % NT;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) srhs[inode[r] * SR + t * 5 + v] = racc[r][v];
+      }
+      __syncthreads();
+      // ---- 2. Y = M_i^-1 RHS.  The last warp streams M_i^-1 through a ring of shared-memory
+      // stages (cp.async.bulk, full/empty mbarriers); the other warps never wait for each
+      // other inside the apply.  Consumer thread (row group rg, time slice t) keeps the 4 x 5
+      // tiles Y[4rg..4rg+3][t][0..4] of two row groups (M_i^-1 is symmetric: row l of a stage
+      // serves column l).
+      float acc[2][4][5];
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int e = 0; e < NC; ++e) acc[r][e] = 0.f;
-      const int na = tid, nb = tid + kF32Threads;
-      for (int b = 0; b < nblk; ++b) {
-        const int s = b % kF32Stages;
-        if (!mbar_wait_bounded(&sbar[s], (phase >> s) & 1u)) {
-          atomicOr(&m.flags[F_TIMEOUT], 1);
-          sAbort = 1;
-        }
-        phase ^= (1u << s);
-        const float* stage = sM + (size_t)s * rows * LDmax;
-        const int l0 = b * rows, rb = min(rows, Ni - l0);
-        for (int lr = 0; lr < rb; ++lr) {
-          const float* rhs = srhs + (l0 + lr) * NC;
-          const float a0 = na < Ni ? stage[lr * LD + na] : 0.f;
-          const float a1 = nb < Ni ? stage[lr * LD + nb] : 0.f;
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int e = 0; e < NC; ++e) {
-            const float x = rhs[e];
-            acc[0][e] += a0 * x;
-            acc[1][e] += a1 * x;
+          for (int v = 0; v < 5; ++v) acc[r][i][v] = 0.f;
+      if (!consumer) {
+        if (lane == 0) {
+          for (int b = 0; b < nblk && !sAbort; ++b) {
+            const int s = b % nstage;
+            if (b >= nstage) {
+              if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+                atomicOr(&m.flags[F_TIMEOUT], 1);
+                sAbort = 1;
+                break;
+              }
+              epar ^= 1u << s;
+            }
+            const int rb = min(kF32Rows, Ni - b * kF32Rows);
+            mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
+            bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
+                     &sfull[s]);
+          }
+          // every stage released by the consumers before the ring is reused
+          for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
+            const int s = b % nstage;
+            if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+              atomicOr(&m.flags[F_TIMEOUT], 1);
+              sAbort = 1;
+              break;
+            }
+            epar ^= 1u << s;
           }
         }
-        __syncthreads();  // every thread is done with stage s
-        if (sAbort) break;
-        if (tid == 0 && b + kF32Stages < nblk) {
-          const int bn = b + kF32Stages;
-          const int rbn = min(rows, Ni - bn * rows);
-          mbar_expect_tx(&sbar[s], (uint32_t)(rbn * LD * 4));
-          bulk_g2s(sM + (size_t)s * rows * LDmax, minv + (size_t)bn * rows * LD, (uint32_t)(rbn * LD * 4), &sbar[s]);
+      } else {
+        for (int b = 0; b < nblk; ++b) {
+          const int s = b % nstage;
+          // lane 0 waits (bounded); the warp follows its verdict, so that no lane leaves the
+          // loop alone; the other lanes then observe the completed phase themselves
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            if (lane == 0) {
+              atomicOr(&m.flags[F_TIMEOUT], 1);
+              sAbort = 1;
+            }
+            break;
+          }
+          (void)mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
+          fpar ^= 1u << s;
+          const float* stage = ring + (size_t)s * stage_floats;
+          const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
+          // one pass per row group; a full stage is unrolled completely
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (!(r == 0 ? act0 : act1)) continue;
+            const float* scol = stage + 4 * (rg0 + r * RGC);
+            const float* xrow = srhs + l0 * SR + tt * 5;
+            if (rb == kF32Rows) {
+#pragma unroll
+              for (int lr = 0; lr < kF32Rows; ++lr) {
+                const float4 a = *reinterpret_cast<const float4*>(scol + lr * LD);
+                const float* x = xrow + lr * SR;
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                  const float xv = x[v];
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) acc[r][i][v] += av[i] * xv;
+                }
+              }
+            } else {
+              for (int lr = 0; lr < rb; ++lr) {
+                const float4 a = *reinterpret_cast<const float4*>(scol + lr * LD);
+                const float* x = xrow + lr * SR;
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                  const float xv = x[v];
+#pragma unroll
+                  for (int i = 0; i < 4; ++i) acc[r][i][v] += av[i] * xv;
+                }
+              }
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sempty[s]);
         }
       }
-      if (sAbort) break;
+      __syncthreads();  // every thread has finished reading RHS and the ring is drained
+      if (sAbort) {
+        // a bounded wait ran out (flags[F_TIMEOUT] is set): wait (bounded) for copies still
+        // in flight into the ring, then leave
+        if (!consumer && lane == 0)
+          for (int s2 = 0; s2 < nstage; ++s2) (void)mbar_wait_bounded(&sfull[s2], (fpar >> s2) & 1u);
+        __syncthreads();
+        return;
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!(r == 0 ? act0 : act1)) continue;
+        const int g = rg0 + r * RGC;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int n = 4 * g + i;
+          if (n < Ni)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) srhs[n * SR + tt * 5 + v] = acc[r][i][v];
+        }
+      }
+      __syncthreads();
       float res = 0.f, qmax = 0.f;
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int n = tid + r * kF32Threads;
         if (n >= Ni) continue;
+        float y[NT][5];
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) y[t][v] = srhs[n * SR + t * 5 + v];
 #pragma unroll
         for (int s2 = 0; s2 < NT; ++s2)
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             float x = uh[r][v];
 #pragma unroll
-            for (int t = 0; t < NT; ++t) x -= sK[s2][t] * acc[r][t * 5 + v];
-            const float old = sq[n * NC + s2 * 5 + v];
+            for (int t = 0; t < NT; ++t) x -= sK[s2][t] * y[t][v];
+            const float old = sq[n * SR + s2 * 5 + v];
             res = fmaxf(res, fabsf(x - old));
             qmax = fmaxf(qmax, fabsf(old));
-            sq[n * NC + s2 * 5 + v] = x;
+            sq[n * SR + s2 * 5 + v] = x;
           }
       }
 #pragma unroll
@@ -365,37 +533,31 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
       conv = res <= tol * fmaxf(1.f, qmax);
       __syncthreads();
     }
-    if (sAbort) {
-      // drain: wait (bounded) for every stage still in flight, then leave
-      if (tid == 0)
-        for (int s = 0; s < kF32Stages; ++s) (void)mbar_wait_bounded(&sbar[s], (phase >> s) & 1u);
-      __syncthreads();
-      return;
-    }
     if (tid == 0) {
       m.iters[c] = it;
       if (!conv) atomicAdd(&m.flags[F_NONCONV], 1);
     }
 
-    // ---- epilogue: volume term (gathered into srhs[n][0..4])
+    // ---- epilogue: volume term vol = sum_k A_k^T sum_d S^_d^T adj(J_k) F_bar_k
+    float vacc[2][5];
+    int vcur[2], vend[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int n = tid + r * kF32Threads;
-      if (n < Ni) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) srhs[n * NC + v] = 0.f;
-        cur[r] = (int)(m.inc_ptr[n0 + n] - m.inc_ptr[n0]);
-        cend[r] = (int)(m.inc_ptr[n0 + n + 1] - m.inc_ptr[n0]);
+      for (int v = 0; v < 5; ++v) vacc[r][v] = 0.f;
+      vcur[r] = vend[r] = 0;
+      if (n < Ni) {
+        vcur[r] = (int)(m.inc_ptr[n0 + n] - m.inc_ptr[n0]);
+        vend[r] = (int)(m.inc_ptr[n0 + n + 1] - m.inc_ptr[n0]);
       }
     }
-    const uint32_t* inc = m.inc + m.inc_ptr[n0];
     const int CHV = kF32Chunk * NT;  // sub-tets per volume chunk (sR holds CH*NT slices)
     for (int kc = 0; kc < S; kc += CHV) {
       const int nk = min(CHV, S - kc);
       for (int kl = warp; kl < nk; kl += kF32Warps) {
-        const int64_t kg = kbase + kc + kl;
-        const uint16_t* Ak = m.A + kg * NP;
-        const float* g = m.geo32 + kg * 12;
+        const float* g = rec_g(kc + kl);
+        const uint16_t* Ak = rec_a(kc + kl);
         if (lane < NP) {
           float accb[3][5];
 #pragma unroll
@@ -417,41 +579,45 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
         }
         __syncwarp();
         if (lane < NP) {
-          float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+          float a5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int d = 0; d < 3; ++d)
 #pragma unroll 4
             for (int j = 0; j < NP; ++j) {
-              const float s = sSo[d][j][lane];
+              const float sv = sSo[d][j][lane];
               const float* b = sB + (d * NP + j) * 5;
 #pragma unroll
-              for (int v = 0; v < 5; ++v) acc[v] += s * b[v];
+              for (int v = 0; v < 5; ++v) a5[v] += sv * b[v];
             }
           float* dst = sR + (kl * NP + lane) * 5;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) dst[v] = acc[v];
+          for (int v = 0; v < 5; ++v) dst[v] = a5[v];
         }
         __syncwarp();
       }
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const int n = tid + r * kF32Threads;
-        if (n >= Ni) continue;
-        while (cur[r] < cend[r]) {
-          const uint32_t w = inc[cur[r]];
+        while (vcur[r] < vend[r]) {
+          const uint32_t w = inc[vcur[r]];
           const int k = (int)(w >> 5) - kc;
           if (k >= nk) break;
-          const int j = (int)(w & 31);
+          const float* src = sR + (k * NP + (int)(w & 31)) * 5;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) srhs[n * NC + v] += sR[(k * NP + j) * 5 + v];
-          ++cur[r];
+          for (int v = 0; v < 5; ++v) vacc[r][v] += src[v];
+          ++vcur[r];
         }
       }
       __syncthreads();
     }
     float* vol = (float*)m.vol;
-    for (int e = tid; e < Ni * 5; e += kF32Threads) vol[(n0 + e / 5) * 5 + e % 5] = srhs[(e / 5) * NC + e % 5];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int n = tid + r * kF32Threads;
+      if (n < Ni)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) vol[(n0 + n) * 5 + v] = vacc[r][v];
+    }
 
     // face slots: q_bar and F_bar . n at every face node (flux of the owning sub-tet)
     const int64_t s0 = m.slot_ptr[c];
@@ -461,17 +627,16 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
     for (int e = tid; e < ns * NF; e += kF32Threads) {
       const int sl = e / NF, a = e % NF;
       const int64_t sg = s0 + sl;
-      const int64_t kg = kbase + m.slot_sub[sg];
+      const int kl = m.slot_sub[sg];
       const int j = m.slot_loc[sg * NF + a];
-      const uint16_t* Ak = m.A + kg * NP;
-      const float* g = m.geo32 + kg * 12;
+      const uint16_t* Ak = rec_a(kl);
+      const float* g = rec_g(kl);
       const double* gs = m.slot_geo + sg * 4;
       const float nx = (float)gs[0], ny = (float)gs[1], nz = (float)gs[2];
       float qb[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, fb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       for (int t = 0; t < NT; ++t) {
-        // physical flux (unit geometry): contract with the identity instead of adj(J)
         float Q[5];
-        const float* qn = sq + Ak[j] * NC + t * 5;
+        const float* qn = sq + Ak[j] * SR + t * 5;
 #pragma unroll
         for (int v = 0; v < 5; ++v) Q[v] = qn[v];
         float gq[3][5];
@@ -482,7 +647,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
 #pragma unroll
             for (int v = 0; v < 5; ++v) gx[d][v] = 0.f;
           for (int l = 0; l < NP; ++l) {
-            const float* ql = sq + Ak[l] * NC + t * 5;
+            const float* ql = sq + Ak[l] * SR + t * 5;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
               const float dd = sD[d][j][l];
@@ -516,21 +681,25 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
       for (int e = tid; e < Ni * 5; e += kF32Threads) {
         const int n = e / 5, v = e % 5;
         float acc = 0.f;
-        for (int t = 0; t < NT; ++t) acc += sW[t] * sq[n * NC + t * 5 + v];
+        for (int t = 0; t < NT; ++t) acc += sW[t] * sq[n * SR + t * 5 + v];
         m.qbar_diag[(n0 + n) * 5 + v] = (double)dt * (double)acc;
       }
     __syncthreads();
   }
 }
 
-// FP32 copy of the sub-tet geometry: [T][12] = adj(J) row-major (9), det J, padding.
-__global__ void geo32_kernel(DevMesh m, int64_t T) {
+// Packed FP32 sub-tet records (see f32_rec_bytes): adj(J) and det J as floats, node ids.
+template <int N>
+__global__ void sub32_kernel(DevMesh m, int64_t T) {
+  constexpr int NP = np_of(N), REC = f32_rec_bytes(N);
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= T) return;
+  float* g = reinterpret_cast<float*>(m.sub32 + k * REC);
 #pragma unroll
-  for (int i = 0; i < 10; ++i) m.geo32[k * 12 + i] = (float)m.geo[k * 10 + i];
-  m.geo32[k * 12 + 10] = 0.f;
-  m.geo32[k * 12 + 11] = 0.f;
+  for (int i = 0; i < 10; ++i) g[i] = (float)m.geo[k * 10 + i];
+  uint16_t* a = reinterpret_cast<uint16_t*>(m.sub32 + k * REC + 40);
+  for (int j = 0; j < NP; ++j) a[j] = m.A[k * NP + j];
+  for (int j = NP; j < (REC - 40) / 2; ++j) a[j] = 0;
 }
 
 }  // namespace afe
