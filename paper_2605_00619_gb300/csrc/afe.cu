@@ -136,6 +136,14 @@ void launch_face(afe_mesh* m) {
 
 template <int N, typename Real>
 afe_status launch_corrector(afe_mesh* m) {
+  if (sizeof(Real) == 4 && m->dm.Nmax <= 2 * 4 * afe::kCorrThreads) {
+    const size_t smem = (size_t)m->dm.Nmax * 5 * sizeof(float);
+    if (smem > 48 * 1024)
+      AFE_CUDA(cudaFuncSetAttribute(afe::corrector_f32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    afe::corrector_f32_kernel<N><<<(unsigned)m->dm.C, afe::kCorrThreads, smem, m->stream>>>(m->dm, m->d_ref);
+    return AFE_OK;
+  }
   size_t smem = ((size_t)m->dm.Nmax * 5 * sizeof(Real) + 7) / 8 * 8;
   if (sizeof(Real) == 4) smem += (size_t)m->dm.Nmax * 5 * sizeof(double);
   // static + dynamic shared memory may exceed the 48 KB default: opt in to the size used

@@ -703,3 +703,154 @@ __global__ void sub32_kernel(DevMesh m, int64_t T) {
 }
 
 }  // namespace afe
+
+namespace afe {
+
+// FP32 corrector (Sec. 4.4): one block of 128 threads per cell.
+//   r = vol - sum_slots 2 area Z^ G          (fixed-order gather, FP32)
+//   du = M_i^-1 r                            (thread g: 4-row tiles 4g..4g+3, M_i^-1 streamed
+//                                             by 16-byte loads, eight rows in flight)
+//   u += du + (T - w_i . du) / |P_i|         (FP64: T = exact cell total of r, see below)
+// The FP64 correction makes the cell's conserved totals change by exactly
+// T = 1^T r = -sum_slots 2 area sum_b (sum_a Z^[a][b]) G[b] (the volume term sums to zero:
+// sum_m grad phi_m = 0), so the matched slots of neighbouring cells cancel in FP64.
+constexpr int kCorrThreads = 128;
+
+template <int N>
+__global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(DevMesh m, const RefData* __restrict__ ref) {
+  constexpr int NF = nf_of(N);
+  extern __shared__ __align__(16) float sr[];  // [Nmax][5]
+  __shared__ float sZ[NF][NF];
+  __shared__ double szs[NF];
+  __shared__ double sred[2][5][kCorrThreads];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NF * NF; e += kCorrThreads) sZ[e / NF][e % NF] = (float)ref->Z[e / NF][e % NF];
+  if (tid < NF) {
+    double z = 0.0;
+    for (int a = 0; a < NF; ++a) z += ref->Z[a][tid];
+    szs[tid] = z;
+  }
+  __syncthreads();
+  const int64_t c = blockIdx.x;
+  if (c >= m.C) return;
+  const int64_t n0 = m.node_ptr[c];
+  const int Ni = (int)(m.node_ptr[c + 1] - n0);
+  const int LD = minv_ld(Ni);
+  const int64_t s0 = m.slot_ptr[c];
+  const int ns = (int)(m.slot_ptr[c + 1] - s0);
+  const float* vol = (const float*)m.vol;
+  const float* sG = (const float*)m.slot_G;
+  // r = vol - face term
+  for (int n = tid; n < Ni; n += kCorrThreads) {
+    float acc[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] = vol[(n0 + n) * 5 + v];
+    for (int64_t p = m.finc_ptr[n0 + n]; p < m.finc_ptr[n0 + n + 1]; ++p) {
+      const uint32_t w = m.finc[p];
+      const int64_t s = s0 + (w >> 4);
+      const int a = w & 15;
+      const float twoA = 2.f * (float)m.slot_geo[s * 4 + 3];
+      const float* g = sG + s * NF * 5;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        float f = 0.f;
+#pragma unroll
+        for (int b = 0; b < NF; ++b) f += sZ[a][b] * g[b * 5 + v];
+        acc[v] -= twoA * f;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sr[n * 5 + v] = acc[v];
+  }
+  // exact FP64 cell total of the update
+  double tot[5] = {0, 0, 0, 0, 0};
+  for (int e = tid; e < ns * NF; e += kCorrThreads) {
+    const int64_t s = s0 + e / NF;
+    const int b = e % NF;
+    const double twoA = 2.0 * m.slot_geo[s * 4 + 3];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tot[v] -= twoA * szs[b] * (double)sG[(s * NF + b) * 5 + v];
+  }
+  __syncthreads();
+  // du = M_i^-1 r, thread g owns rows 4g..4g+3 (and 4(g+128).. for cells over 512 nodes)
+  const float* minv = m.minv32 + m.minv_ptr[c];
+  double wdu[5] = {0, 0, 0, 0, 0};
+  float du[2][4][5];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int g = tid + r * kCorrThreads;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) du[r][i][v] = 0.f;
+    if (4 * g >= Ni) continue;
+    const float* col = minv + 4 * g;
+    for (int l0 = 0; l0 < Ni; l0 += 8) {
+      float4 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        a[u] = l0 + u < Ni ? __ldcs(reinterpret_cast<const float4*>(col + (size_t)(l0 + u) * LD))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (l0 + u >= Ni) break;
+        const float* x = sr + (l0 + u) * 5;
+        const float av[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const float xv = x[v];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) du[r][i][v] += av[i] * xv;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int n = 4 * g + i;
+      if (n >= Ni) break;
+      const double w = m.wvec[n0 + n];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) wdu[v] += w * (double)du[r][i][v];
+    }
+  }
+  // fixed-order block reductions of T and w . du
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    sred[0][v][tid] = tot[v];
+    sred[1][v][tid] = wdu[v];
+  }
+  __syncthreads();
+  for (int st = kCorrThreads / 2; st > 0; st >>= 1) {
+    if (tid < st)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        sred[0][v][tid] += sred[0][v][tid + st];
+        sred[1][v][tid] += sred[1][v][tid + st];
+      }
+    __syncthreads();
+  }
+  double corr[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) corr[v] = (sred[0][v][0] - sred[1][v][0]) / m.cell_vol[c];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int g = tid + r * kCorrThreads;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int n = 4 * g + i;
+      if (n >= Ni) break;
+      double* un = m.u + (n0 + n) * 5;
+      bool bad = false;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        un[v] += (double)du[r][i][v] + corr[v];
+        bad |= !isfinite(un[v]);
+      }
+      const double rho = un[0];
+      const double p = (m.gamma - 1.0) * (un[4] - 0.5 * (un[1] * un[1] + un[2] * un[2] + un[3] * un[3]) / rho);
+      if (bad || !(rho > 0.0) || !(p > 0.0)) atomicOr(&m.flags[F_NONFINITE], 8);
+    }
+  }
+}
+
+}  // namespace afe
