@@ -8,6 +8,7 @@ corrector).  ``value`` is the reduced-precision form (FP32 arithmetic, FP64 mast
 FP64 time step and conservative cell totals); the plain FP64 form is timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --serve      (continuous-batching serving run; see serve())
 
 N > 1 (torchrun): every rank runs an independent simulation (mesh seed = rank); there is
 no data-path collective and ``value`` is the sum over ranks of DOF-updates over the max
@@ -43,6 +44,10 @@ def _args():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 form (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load, requests per second")
+    ap.add_argument("--serve-slots", type=int, default=16, help="slots per catalogue mesh")
     return ap.parse_args()
 
 
@@ -242,7 +247,9 @@ def ours(args):
         pass
 
     def run_form(prec, steps, warmup, e2e):
-        p = afe.afe_default_params(args.order, precision=prec, picard_tol=1e-6 if prec == afe.AFE_FP32 else 1e-12)
+        fp32 = prec == afe.AFE_FP32
+        p = afe.afe_default_params(args.order, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
+                                   picard_max=128 if fp32 else 64)
         h = afe.create_from_polymesh(pm, p, stream=sid)
         n_nodes = afe.afe_num_nodes(h)
         node_ptr = afe.afe_node_ptr(h, pm.n_cells)
@@ -333,12 +340,12 @@ def ours(args):
         ach = r32["flops"] / (pred_ms / 1e3) / 1e12
         out["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                            "frac": ach / fp32_peak, "traffic": None,
-                           "kernel": "predictor_kernel<3,float>",
+                           "kernel": f"predictor_f32_kernel<{args.order}>",
                            "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"}
     else:
         ach = r32["abytes"] / (pred_ms / 1e3) / 1e9
         out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                           "traffic": None, "kernel": "predictor_kernel<3,float>", "peak_note": "of measured"}
+                           "traffic": None, "kernel": f"predictor_f32_kernel<{args.order}>", "peak_note": "of measured"}
     out["roofline"]["algorithmic_flops"] = r32["flops"]
     out["roofline"]["algorithmic_bytes"] = r32["abytes"]
     if r64 is not None:
@@ -366,8 +373,68 @@ def ours(args):
         dist.destroy_process_group()
 
 
+def serve(args):
+    """Continuous batching of many small simulations (one GPU).
+
+    Catalogue: periodic jittered-Voronoi meshes with 4^3, 5^3 and 6^3 cells, AFE N (default
+    3), FP32 form, Euler, CFL 0.3, density-wave initial data; ``--serve-slots`` resident
+    handles per mesh.  Requests arrive as a Poisson process of ``--serve-rate`` per second,
+    each for a mesh drawn uniformly and 5, 10 or 20 CFL steps.  The batched server (all
+    occupied slots advanced together, one launch per stage, CUDA graph per batch) is timed
+    against the serial server (one request at a time, alone) on the same requests.  Reported:
+    DOF-updates/s over the run, p50/p99 request latency (arrival to completion).
+    """
+    import torch
+
+    from inputs import states
+    from inputs.voronoi import periodic_voronoi
+    from paper_2605_00619_gb300 import afe
+    from paper_2605_00619_gb300.serving import GpuEngine, Server, poisson_requests
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    afe.lib()
+    cat = {f"{n}^3": periodic_voronoi(n, seed=10 + n) for n in (4, 5, 6)}
+    p = afe.afe_default_params(args.order, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+    stream = torch.cuda.Stream()
+    eng = GpuEngine(cat, {k: args.serve_slots for k in cat}, p, stream=stream.cuda_stream)
+    for sl in eng.slots:
+        if sl.mesh not in eng.default_state:
+            eng.default_state[sl.mesh] = states.density_wave(afe.afe_get_node_coords(sl.handle))
+    keys = sorted(cat)
+    warm = poisson_requests(0.0, 2 * len(eng.slots), keys, [3], seed=99)
+    Server(eng).run(warm)
+    Server(eng, mode="serial").run(warm[:len(keys)])
+    reqs = lambda: poisson_requests(args.serve_rate, args.serve_requests, keys, [5, 10, 20], seed=1)  # noqa: E731
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    sb = Server(eng, max_chunk=4).run(reqs())
+    clk = clocks.stop()
+    ss = Server(eng, mode="serial").run(reqs())
+    nodes = {k: next(s.n_nodes for s in eng.slots if s.mesh == k) for k in keys}
+    out = {
+        "metric": "serving throughput, continuous batching", "value": sb.throughput, "unit": UNIT,
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "p50_ms": 1e3 * sb.p50_s, "p99_ms": 1e3 * sb.p99_s, "mean_ms": 1e3 * sb.mean_s,
+        "mean_batch_members": sb.mean_batch, "batch_steps": sb.steps_launched, "failed": sb.failed,
+        "makespan_s": sb.makespan_s,
+        "serial": {"value": ss.throughput, "unit": UNIT, "p50_ms": 1e3 * ss.p50_s, "p99_ms": 1e3 * ss.p99_s,
+                   "makespan_s": ss.makespan_s, "failed": ss.failed},
+        "batched_over_serial": sb.throughput / ss.throughput,
+        "clocks": clk,
+        "config": {"workload": f"Poisson arrivals at {args.serve_rate:g}/s, {args.serve_requests} requests of 5/10/20 "
+                               f"CFL steps on periodic Voronoi meshes {', '.join(keys)} (nodes "
+                               f"{', '.join(str(nodes[k]) for k in keys)}), AFE N={args.order}, FP32 form, Euler",
+                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes},
+    }
+    eng.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
+    if args.serve:
+        serve(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -78,8 +78,9 @@ typedef struct {
   int64_t steps;        /* completed steps                                       */
   double picard_mean;   /* mean predictor iterations over cells, last step       */
   int32_t picard_max;   /* max predictor iterations over cells, last step        */
-  int64_t nonconverged; /* cells that hit picard_max, last step                  */
-  int64_t troubled;     /* cells with beta_i > 0, last step                      */
+  int64_t nonconverged; /* cell-steps that hit picard_max since the last afe_step /
+                           afe_sync (one step after afe_step)                     */
+  int64_t troubled;     /* cell-steps with beta_i > 0, same span                  */
   double totals[5];     /* sum_i 1^T M_i u_i per conserved variable (FP64)       */
   int64_t kernel_launches; /* kernels launched by afe_step / afe_step_async so far */
 } afe_stats;
@@ -150,8 +151,9 @@ afe_status afe_compute_dt(afe_mesh* m, double* dt);
 afe_status afe_step(afe_mesh* m, double dt);
 
 /* `nsteps` steps enqueued back to back on the handle's stream with no host synchronisation
- * between them (dt as in afe_step); returns after enqueueing.  Status flags accumulate and
- * are reported by afe_get_stats / afe_sync. */
+ * between them (dt as in afe_step); returns after enqueueing.  Status flags accumulate over
+ * the steps enqueued since the last afe_step / afe_sync and are reported by afe_get_stats /
+ * afe_sync. */
 afe_status afe_step_async(afe_mesh* m, double dt, int nsteps);
 
 /* Wait for the handle's stream and return the accumulated status of afe_step_async calls
@@ -199,6 +201,48 @@ afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset);
 #define AFE_NOALLOC_MAX_NODES ((int64_t)AFE_NOALLOC_CHUNK * AFE_NOALLOC_MAX_PARTIALS)
 afe_status afe_conserved_totals_noalloc(const afe_mesh* m, const double* dq, double* dtotals,
                                         void* cuda_stream);
+
+/* ---- Several simulations advanced together ------------------------------------------
+ * The paper advances one mesh; it has no counterpart for this.  A batch advances up to
+ * AFE_MAX_BATCH independent handles -- each with its own mesh, state, parameters, dt and
+ * time -- with one kernel launch per stage over all their cells, so that many small
+ * simulations occupy the GPU the way one large mesh does.  Every kernel works per cell, per
+ * polygonal face or per member, and the CFL maximum is an order-independent integer
+ * atomicMax, so each member's result is bit-identical to stepping it alone.
+ * Requirements (else AFE_EINVAL): every member AFE_FP32 with the same order N, on the
+ * current device, with cells small enough for the shared-memory FP32 kernels, and the
+ * members' largest cells fitting that shared-memory plan together.
+ * Ownership: members keep owning their memory and must outlive the batch; the batch owns a
+ * work counter, its CUDA graph and, when created with cuda_stream NULL, a non-blocking
+ * stream of its own.  afe_batch_create waits for the members' streams; afterwards the batch
+ * orders all its work on its stream, so a member must not be stepped on its own between
+ * afe_batch_step_async and afe_batch_sync. */
+#define AFE_MAX_BATCH 64
+typedef struct afe_batch afe_batch;
+
+afe_status afe_batch_create(afe_mesh* const* members, int n_members, void* cuda_stream,
+                            afe_batch** out);
+
+/* Enqueue `nsteps` steps of every member (dt <= 0: each member its own CFL step; dt > 0: that
+ * step for all).  use_graph != 0: one step is captured into a CUDA graph on first use (again
+ * when dt changes) and the graph is launched nsteps times; otherwise the kernels are
+ * launched directly.  Returns after enqueueing; status flags accumulate until
+ * afe_batch_sync. */
+afe_status afe_batch_step_async(afe_batch* b, double dt, int nsteps, int use_graph);
+
+/* Wait for the batch stream.  member_status[n_members] (NULL to skip) receives each member's
+ * status over the steps since the last sync (AFE_OK, AFE_ENOCONV, AFE_ENONFINITE or
+ * AFE_ETIMEOUT); the return value is the most severe of them.  Each member's time, step
+ * count and last dt (afe_get_stats) are brought up to date. */
+afe_status afe_batch_sync(afe_batch* b, int* member_status);
+
+/* Total cells and nodes of the members, kernels launched so far (counted one by one, also
+ * when they ran inside graphs) and graph launches (NULL to skip any). */
+afe_status afe_batch_info(const afe_batch* b, int64_t* n_cells, int64_t* n_nodes,
+                          int64_t* launches, int64_t* graph_launches);
+
+/* Wait for the batch stream and release the batch (not its members; NULL is ignored). */
+void afe_batch_destroy(afe_batch* b);
 
 /* Bytes of device memory held by the handle. */
 afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes);

@@ -94,6 +94,11 @@ _SIGS = {
     "afe_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "afe_conserved_totals_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "afe_stage_times": (ctypes.c_int, [_P, _D, _I64, ctypes.c_int]),
+    "afe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "afe_batch_step_async": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "afe_batch_sync": (ctypes.c_int, [_P, _I32]),
+    "afe_batch_info": (ctypes.c_int, [_P, _I64, _I64, _I64, _I64]),
+    "afe_batch_destroy": (None, [_P]),
     "afe_last_error": (ctypes.c_char_p, []),
     "afe_mesh_destroy": (None, [_P]),
 }
@@ -286,6 +291,45 @@ def afe_conserved_totals_noalloc(m, dq_ptr: int, dtotals_ptr: int, stream: int =
     """Conserved totals of a device state into a device array of 5 doubles, with no device
     allocation by the call (for callers that may not allocate at the point of use)."""
     return _check(lib().afe_conserved_totals_noalloc(m, _P(dq_ptr), _P(dtotals_ptr), _P(stream)), check)
+
+
+AFE_MAX_BATCH = 64
+
+
+def afe_batch_create(members, stream: int = 0, check: bool = True):
+    """Batch of mesh handles stepped by one launch per stage; returns an opaque handle, or
+    (None, status) with check=False."""
+    arr = (_P * len(members))(*[m.value if isinstance(m, _P) else m for m in members])
+    out = _P()
+    st = lib().afe_batch_create(arr, len(members), _P(stream), ctypes.byref(out))
+    if not check:
+        return (out if st == AFE_OK else None), st
+    _check(st)
+    return out
+
+
+def afe_batch_step_async(b, dt: float = 0.0, nsteps: int = 1, use_graph: bool = True):
+    _check(lib().afe_batch_step_async(b, float(dt), int(nsteps), int(bool(use_graph))))
+
+
+def afe_batch_sync(b, n_members: int, check: bool = True):
+    """Returns (status, per-member statuses as a numpy int32 array)."""
+    ms = np.zeros(n_members, np.int32)
+    st = lib().afe_batch_sync(b, ms.ctypes.data_as(_I32))
+    _check(st, check)
+    return st, ms
+
+
+def afe_batch_info(b):
+    """Returns (cells, nodes, kernel launches, graph launches)."""
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().afe_batch_info(b, *[ctypes.byref(x) for x in v]))
+    return tuple(int(x.value) for x in v)
+
+
+def afe_batch_destroy(b):
+    if b:
+        lib().afe_batch_destroy(b)
 
 
 def afe_mesh_destroy(m):

@@ -43,6 +43,7 @@ struct afe_mesh {
   afe::Topology topo;
   afe::DevMesh dm{};
   afe::RefData* d_ref = nullptr;
+  afe::Batch self{};  // this mesh as a batch of one (its DevMesh record is kept in step with dm)
   std::vector<void*> allocs;
   int64_t bytes = 0;
   void* scratch = nullptr;
@@ -96,15 +97,49 @@ namespace {
     if (s_ != AFE_OK) return s_;     \
   } while (0)
 
+// One launch sequence: the batch table plus what the launches need besides it.  A single
+// mesh runs as a batch of one; the FP64 kernels (and the FP32 fall-backs for cells too large
+// for shared memory) take the single mesh's record directly.
+struct StepPlan {
+  const afe::Batch* b = nullptr;
+  cudaStream_t st = nullptr;
+  int order = 1, fp32 = 0, limiter = 0, n_sm = 1, diag = 0;
+  int f32_ok = 0;
+  size_t f32_smem = 0;
+  const afe::RefData* d_ref = nullptr;
+  afe_mesh* single = nullptr;  // nullptr for a batch (FP32 shared-memory kernels only)
+  afe_mesh* prof = nullptr;    // stage events are recorded on this mesh when profiling
+};
+
+StepPlan plan_of(afe_mesh* m) {
+  StepPlan P;
+  P.b = &m->self;
+  P.st = m->stream;
+  P.order = m->p.order;
+  P.fp32 = m->p.precision == AFE_FP32;
+  P.limiter = m->p.limiter;
+  P.n_sm = m->n_sm;
+  P.diag = m->diag;
+  P.f32_ok = m->f32_ok;
+  P.f32_smem = m->f32_smem;
+  P.d_ref = m->d_ref;
+  P.single = m;
+  P.prof = m;
+  return P;
+}
+
+bool corrector_f32_fits(int Nmax) { return Nmax <= 2 * 4 * afe::kCorrThreads; }
+
 template <int N, typename Real>
-void launch_predictor(afe_mesh* m) {
-  if (sizeof(Real) == 4 && m->f32_ok) {
-    afe::predictor_f32_kernel<N><<<m->n_sm, afe::kF32Threads, m->f32_smem, m->stream>>>(m->dm, m->d_ref, m->diag,
-                                                                                        (int)m->f32_smem);
+void launch_predictor(const StepPlan& P) {
+  if (sizeof(Real) == 4 && P.f32_ok) {
+    afe::predictor_f32_kernel<N><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
+                                                                               (int)P.f32_smem);
     return;
   }
-  afe::predictor_kernel<N, Real><<<m->pred_grid, 256, 0, m->stream>>>(m->dm, m->d_ref, (Real*)m->scratch,
-                                                                      m->scratch_stride, m->diag);
+  afe_mesh* m = P.single;
+  afe::predictor_kernel<N, Real><<<m->pred_grid, 256, 0, P.st>>>(m->dm, m->d_ref, (Real*)m->scratch,
+                                                                 m->scratch_stride, P.diag);
 }
 
 // Shared-memory plan of the FP32 predictor; cells too large for it use the global-scratch kernel.
@@ -128,48 +163,49 @@ afe_status plan_f32(afe_mesh* m) {
 }
 
 template <int N, typename Real>
-void launch_face(afe_mesh* m) {
-  const int64_t threads = m->dm.n_groups * 32;
+void launch_face(const StepPlan& P) {
+  const int64_t threads = P.b->gpre[P.b->nh] * 32;
   const int blocks = (int)((threads + 255) / 256);
-  if (blocks > 0) afe::face_kernel<N, Real><<<blocks, 256, 0, m->stream>>>(m->dm);
+  if (blocks > 0) afe::face_kernel<N, Real><<<blocks, 256, 0, P.st>>>(*P.b);
 }
 
 template <int N, typename Real>
-afe_status launch_corrector(afe_mesh* m) {
-  if (sizeof(Real) == 4 && m->dm.Nmax <= 2 * 4 * afe::kCorrThreads) {
-    const size_t smem = (size_t)m->dm.Nmax * 5 * sizeof(float);
+afe_status launch_corrector(const StepPlan& P) {
+  if (sizeof(Real) == 4 && corrector_f32_fits(P.b->Nmax)) {
+    const size_t smem = (size_t)P.b->Nmax * 5 * sizeof(float);
     if (smem > 48 * 1024)
       AFE_CUDA(cudaFuncSetAttribute(afe::corrector_f32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-    afe::corrector_f32_kernel<N><<<(unsigned)m->dm.C, afe::kCorrThreads, smem, m->stream>>>(m->dm, m->d_ref);
+    afe::corrector_f32_kernel<N><<<(unsigned)P.b->cpre[P.b->nh], afe::kCorrThreads, smem, P.st>>>(*P.b, P.d_ref);
     return AFE_OK;
   }
+  afe_mesh* m = P.single;
   size_t smem = ((size_t)m->dm.Nmax * 5 * sizeof(Real) + 7) / 8 * 8;
   if (sizeof(Real) == 4) smem += (size_t)m->dm.Nmax * 5 * sizeof(double);
   // static + dynamic shared memory may exceed the 48 KB default: opt in to the size used
   AFE_CUDA(cudaFuncSetAttribute(afe::corrector_kernel<N, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)std::min<int64_t>(m->dm.C, (int64_t)m->n_sm * 4);
-  afe::corrector_kernel<N, Real><<<grid, 256, smem, m->stream>>>(m->dm, m->d_ref);
+  afe::corrector_kernel<N, Real><<<grid, 256, smem, P.st>>>(m->dm, m->d_ref);
   return AFE_OK;
 }
 
 template <typename Real>
-afe_status dispatch_stage(afe_mesh* m, int stage) {
-  switch (m->p.order) {
+afe_status dispatch_stage(const StepPlan& P, int stage) {
+  switch (P.order) {
     case 1:
-      if (stage == 0) launch_predictor<1, Real>(m);
-      else if (stage == 1) launch_face<1, Real>(m);
-      else return launch_corrector<1, Real>(m);
+      if (stage == 0) launch_predictor<1, Real>(P);
+      else if (stage == 1) launch_face<1, Real>(P);
+      else return launch_corrector<1, Real>(P);
       break;
     case 2:
-      if (stage == 0) launch_predictor<2, Real>(m);
-      else if (stage == 1) launch_face<2, Real>(m);
-      else return launch_corrector<2, Real>(m);
+      if (stage == 0) launch_predictor<2, Real>(P);
+      else if (stage == 1) launch_face<2, Real>(P);
+      else return launch_corrector<2, Real>(P);
       break;
     case 3:
-      if (stage == 0) launch_predictor<3, Real>(m);
-      else if (stage == 1) launch_face<3, Real>(m);
-      else return launch_corrector<3, Real>(m);
+      if (stage == 0) launch_predictor<3, Real>(P);
+      else if (stage == 1) launch_face<3, Real>(P);
+      else return launch_corrector<3, Real>(P);
       break;
     default:
       return fail(AFE_EINVAL, "order must be 1, 2 or 3");
@@ -177,56 +213,61 @@ afe_status dispatch_stage(afe_mesh* m, int stage) {
   return AFE_OK;
 }
 
-afe_status stage(afe_mesh* m, int s) {
-  return m->p.precision == AFE_FP32 ? dispatch_stage<float>(m, s) : dispatch_stage<double>(m, s);
-}
+afe_status stage(const StepPlan& P, int s) { return P.fp32 ? dispatch_stage<float>(P, s) : dispatch_stage<double>(P, s); }
 
 // limiter (if on) and the time step, all on the device
-afe_status enqueue_dt(afe_mesh* m, double dt) {
-  const int cgrid = (int)std::min<int64_t>(m->dm.C, (int64_t)m->n_sm * 8);
-  if (m->p.limiter) {
-    afe::cell_means_kernel<<<cgrid, 256, 0, m->stream>>>(m->dm);
-    afe::limiter_kernel<<<(int)((m->dm.C + 127) / 128), 128, 0, m->stream>>>(m->dm);
+afe_status enqueue_dt(const StepPlan& P, double dt) {
+  const int64_t C = P.b->cpre[P.b->nh];
+  if (P.limiter) {
+    const int cgrid = (int)std::min<int64_t>(C, (int64_t)P.n_sm * 8);
+    afe::cell_means_kernel<<<cgrid, 256, 0, P.st>>>(*P.b);
+    afe::limiter_kernel<<<(int)((C + 127) / 128), 128, 0, P.st>>>(*P.b);
   }
   if (dt > 0) {
-    afe::set_dt_kernel<<<1, 1, 0, m->stream>>>(m->dm, dt);
+    afe::set_dt_kernel<<<1, 64, 0, P.st>>>(*P.b, dt);
   } else {
-    AFE_CUDA(cudaMemsetAsync(m->dm.maxbits, 0, sizeof(unsigned long long), m->stream));
-    afe::cfl_kernel<<<cgrid, 128, 0, m->stream>>>(m->dm);
-    afe::dt_finalize_kernel<<<1, 1, 0, m->stream>>>(m->dm);
+    afe::cfl_kernel<<<(int)((C * 32 + 255) / 256), 256, 0, P.st>>>(*P.b);
+    afe::dt_finalize_kernel<<<1, 64, 0, P.st>>>(*P.b);
   }
   return AFE_OK;
 }
 
-afe_status record(afe_mesh* m, int k) {
-  if (!m->profiling) return AFE_OK;
+afe_status record(const StepPlan& P) {
+  afe_mesh* m = P.prof;
+  if (!m || !m->profiling) return AFE_OK;
   if (m->ev_used >= m->ev.size()) {
     cudaEvent_t e;
     AFE_CUDA(cudaEventCreate(&e));
     m->ev.push_back(e);
   }
-  (void)k;
-  AFE_CUDA(cudaEventRecord(m->ev[m->ev_used++], m->stream));
+  AFE_CUDA(cudaEventRecord(m->ev[m->ev_used++], P.st));
+  return AFE_OK;
+}
+
+// kernels per step: begin + [means + limiter] + (set_dt | cfl + finalize) + predictor + face
+// + corrector + clock
+int launches_per_step(const StepPlan& P, double dt) { return 1 + (P.limiter ? 2 : 0) + (dt > 0 ? 1 : 2) + 3 + 1; }
+
+afe_status enqueue_step(const StepPlan& P, double dt) {
+  afe::step_begin_kernel<<<1, 64, 0, P.st>>>(*P.b);
+  AFE_TRY(record(P));
+  AFE_TRY(enqueue_dt(P, dt));
+  AFE_TRY(record(P));
+  AFE_TRY(stage(P, 0));
+  AFE_TRY(record(P));
+  AFE_TRY(stage(P, 1));
+  AFE_TRY(record(P));
+  AFE_TRY(stage(P, 2));
+  AFE_TRY(record(P));
+  afe::advance_time_kernel<<<1, 64, 0, P.st>>>(*P.b);
+  AFE_CUDA(cudaGetLastError());
   return AFE_OK;
 }
 
 afe_status enqueue_step(afe_mesh* m, double dt) {
-  // kernels per step: [means + limiter] + (set_dt | cfl + finalize) + predictor + face + corrector + clock
-  m->launches += (m->p.limiter ? 2 : 0) + (dt > 0 ? 1 : 2) + 3 + 1;
-  AFE_CUDA(cudaMemsetAsync(m->dm.flags, 0, afe::F_COUNT * sizeof(int), m->stream));
-  AFE_TRY(record(m, 0));
-  AFE_TRY(enqueue_dt(m, dt));
-  AFE_CUDA(cudaMemsetAsync(m->dm.work, 0, sizeof(int), m->stream));
-  AFE_TRY(record(m, 1));
-  AFE_TRY(stage(m, 0));
-  AFE_TRY(record(m, 2));
-  AFE_TRY(stage(m, 1));
-  AFE_TRY(record(m, 3));
-  AFE_TRY(stage(m, 2));
-  AFE_TRY(record(m, 4));
-  afe::advance_time_kernel<<<1, 1, 0, m->stream>>>(m->dm);
-  AFE_CUDA(cudaGetLastError());
-  return AFE_OK;
+  const StepPlan P = plan_of(m);
+  m->launches += launches_per_step(P, dt);
+  return enqueue_step(P, dt);
 }
 
 afe_status read_flags(afe_mesh* m, int* flags) {
@@ -242,6 +283,20 @@ afe_status status_of(const int* flags) {
   if (flags[afe::F_NONCONV])
     return fail(AFE_ENOCONV, std::to_string(flags[afe::F_NONCONV]) + " cells hit picard_max");
   return AFE_OK;
+}
+
+// Refreshes the batch-of-one record read by the batch-aware kernels.
+void sync_self(afe_mesh* m) {
+  afe::Batch& b = m->self;
+  b.nh = 1;
+  b.Nmax = m->topo.Nmax;
+  b.Smax = m->topo.Smax;
+  b.work = m->dm.work;
+  b.cpre[0] = 0;
+  b.cpre[1] = m->topo.C;
+  b.gpre[0] = 0;
+  b.gpre[1] = m->topo.n_groups;
+  b.tab[0] = m->dm;
 }
 
 afe_status check_params(const afe_params* p) {
@@ -385,6 +440,7 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
   AFE_TRY(M->alloc(&d.flags, afe::F_COUNT));
   AFE_TRY(M->alloc(&d.work, 1));
   AFE_TRY(M->alloc(&M->d_ref, 1));
+
   AFE_TRY(M->alloc(&M->d_totals_partial, (size_t)M->totals_blocks * 5));
   AFE_TRY(M->alloc(&M->d_totals, 5));
   AFE_CUDA(cudaMemcpy(M->d_ref, &M->ref, sizeof(afe::RefData), cudaMemcpyHostToDevice));
@@ -448,6 +504,7 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
         break;
       }
   }
+  sync_self(M);
   *out = m.release();
   return AFE_OK;
 }
@@ -529,8 +586,10 @@ afe_status afe_get_state_device(const afe_mesh* m, double* dq) {
 
 afe_status afe_compute_dt(afe_mesh* m, double* dt) {
   if (!m || !dt) return fail(AFE_EINVAL, "NULL argument");
-  AFE_CUDA(cudaMemsetAsync(m->dm.flags, 0, afe::F_COUNT * sizeof(int), m->stream));
-  AFE_TRY(enqueue_dt(m, -1.0));
+  const StepPlan P = plan_of(m);
+  afe::flags_clear_kernel<<<1, 64, 0, P.st>>>(*P.b);
+  afe::step_begin_kernel<<<1, 64, 0, P.st>>>(*P.b);
+  AFE_TRY(enqueue_dt(P, -1.0));
   AFE_CUDA(cudaMemcpyAsync(dt, m->dm.dt, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   int flags[afe::F_COUNT];
   AFE_TRY(read_flags(m, flags));
@@ -539,6 +598,8 @@ afe_status afe_compute_dt(afe_mesh* m, double* dt) {
 
 afe_status afe_step(afe_mesh* m, double dt) {
   if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  afe::flags_clear_kernel<<<1, 64, 0, m->stream>>>(m->self);
+  m->launches += 1;
   AFE_TRY(enqueue_step(m, dt));
   int flags[afe::F_COUNT];
   double hdt = 0;
@@ -552,6 +613,10 @@ afe_status afe_step(afe_mesh* m, double dt) {
 
 afe_status afe_step_async(afe_mesh* m, double dt, int nsteps) {
   if (!m || nsteps < 0) return fail(AFE_EINVAL, "bad argument");
+  if (m->pending == 0 && nsteps > 0) {  // a new series: its status starts clean
+    afe::flags_clear_kernel<<<1, 64, 0, m->stream>>>(m->self);
+    m->launches += 1;
+  }
   for (int i = 0; i < nsteps; ++i) {
     AFE_TRY(enqueue_step(m, dt));
     // fold this step's flags into the pending status without a host round trip
@@ -607,7 +672,11 @@ afe_status afe_get_stats(const afe_mesh* mc, afe_stats* s) {
 
 afe_status afe_set_diagnostics(afe_mesh* m, int on) {
   if (!m) return fail(AFE_EINVAL, "NULL mesh");
-  if (on && !m->dm.qbar_diag) AFE_TRY(m->alloc(&m->dm.qbar_diag, m->topo.n_nodes * 5));
+  if (on && !m->dm.qbar_diag) {
+    AFE_CUDA(cudaStreamSynchronize(m->stream));
+    AFE_TRY(m->alloc(&m->dm.qbar_diag, m->topo.n_nodes * 5));
+    sync_self(m);
+  }
   m->diag = on ? 1 : 0;
   return AFE_OK;
 }
@@ -651,6 +720,208 @@ afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes) {
   if (!m || !bytes) return fail(AFE_EINVAL, "NULL argument");
   *bytes = m->bytes;
   return AFE_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------------------
+// Batches: several handles advanced by one launch per stage (afe_batch_*).
+
+struct afe_batch {
+  std::vector<afe_mesh*> mem;
+  afe::Batch bt{};
+  int* d_work = nullptr;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  StepPlan plan;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double graph_dt = 0.0;
+  bool have_graph = false;
+  int pending = 0;
+  int64_t launches = 0, graph_launches = 0;
+  ~afe_batch() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (d_work) cudaFree(d_work);
+    if (own_stream && st) cudaStreamDestroy(st);
+  }
+};
+
+namespace {
+
+size_t f32_need(int order, int Nmax, int Smax) { return afe::predictor_f32_smem(order, Nmax, Smax); }
+
+afe_status batch_capture(afe_batch* b, double dt) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->have_graph = false;
+  AFE_CUDA(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+  afe_status s = enqueue_step(b->plan, dt);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->st, &g);
+  if (s != AFE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(AFE_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  b->graph = g;
+  AFE_CUDA(cudaGraphInstantiate(&b->gexec, g, 0));
+  b->graph_dt = dt;
+  b->have_graph = true;
+  return AFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+afe_status afe_batch_create(afe_mesh* const* members, int n_members, void* cuda_stream, afe_batch** out) {
+  if (!out) return fail(AFE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!members || n_members < 1 || n_members > AFE_MAX_BATCH)
+    return fail(AFE_EINVAL, "a batch holds 1 to " + std::to_string(AFE_MAX_BATCH) + " members");
+  static_assert(AFE_MAX_BATCH <= afe::kMaxBatch, "batch table too small");
+  std::unique_ptr<afe_batch> b(new afe_batch());
+  int64_t C = 0, G = 0;
+  int Nmax = 0, Smax = 0;
+  for (int h = 0; h < n_members; ++h) {
+    afe_mesh* m = members[h];
+    if (!m) return fail(AFE_EINVAL, "member " + std::to_string(h) + " is NULL");
+    for (int k = 0; k < h; ++k)
+      if (members[k] == m) return fail(AFE_EINVAL, "a handle appears twice in the batch");
+    if (m->p.precision != AFE_FP32) return fail(AFE_EINVAL, "batch members must use AFE_FP32");
+    if (m->p.order != members[0]->p.order) return fail(AFE_EINVAL, "batch members must share the order N");
+    if (m->device != members[0]->device) return fail(AFE_EINVAL, "batch members must live on one device");
+    if (!m->f32_ok || !corrector_f32_fits(m->topo.Nmax))
+      return fail(AFE_EINVAL, "member " + std::to_string(h) + " has cells too large for the batched kernels");
+    AFE_CUDA(cudaStreamSynchronize(m->stream));
+    b->bt.cpre[h] = C;
+    b->bt.gpre[h] = G;
+    b->bt.tab[h] = m->dm;
+    C += m->topo.C;
+    G += m->topo.n_groups;
+    Nmax = std::max(Nmax, m->topo.Nmax);
+    Smax = std::max(Smax, m->topo.Smax);
+  }
+  b->bt.cpre[n_members] = C;
+  b->bt.gpre[n_members] = G;
+  b->bt.nh = n_members;
+  b->bt.Nmax = Nmax;
+  b->bt.Smax = Smax;
+  afe_mesh* m0 = members[0];
+  if (f32_need(m0->p.order, Nmax, Smax) > m0->f32_smem)
+    return fail(AFE_EINVAL, "the members' largest cells do not fit the shared-memory plan together");
+  if (C > (int64_t)INT32_MAX) return fail(AFE_EINVAL, "too many cells in one batch");
+  int dev = -1;
+  AFE_CUDA(cudaGetDevice(&dev));
+  if (dev != m0->device) return fail(AFE_EINVAL, "the current device is not the members' device");
+  {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(int));
+    if (e != cudaSuccess) return fail(AFE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    b->d_work = (int*)p;
+  }
+  b->bt.work = b->d_work;
+  if (cuda_stream) {
+    b->st = (cudaStream_t)cuda_stream;
+  } else {
+    AFE_CUDA(cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  b->mem.assign(members, members + n_members);
+  StepPlan& P = b->plan;
+  P.b = &b->bt;
+  P.st = b->st;
+  P.order = m0->p.order;
+  P.fp32 = 1;
+  P.limiter = 0;
+  for (afe_mesh* m : b->mem) P.limiter |= m->p.limiter ? 1 : 0;
+  P.n_sm = m0->n_sm;
+  P.diag = 0;
+  P.f32_ok = 1;
+  P.f32_smem = m0->f32_smem;
+  P.d_ref = m0->d_ref;
+  P.single = nullptr;
+  P.prof = nullptr;
+  *out = b.release();
+  return AFE_OK;
+}
+
+afe_status afe_batch_step_async(afe_batch* b, double dt, int nsteps, int use_graph) {
+  if (!b || nsteps < 0) return fail(AFE_EINVAL, "bad argument");
+  if (nsteps == 0) return AFE_OK;
+  if (b->pending == 0) {
+    afe::flags_clear_kernel<<<1, 64, 0, b->st>>>(b->bt);
+    AFE_CUDA(cudaGetLastError());
+    b->launches += 1;
+  }
+  const int per = launches_per_step(b->plan, dt);
+  if (use_graph) {
+    if (!b->have_graph || b->graph_dt != dt) AFE_TRY(batch_capture(b, dt));
+    for (int i = 0; i < nsteps; ++i) AFE_CUDA(cudaGraphLaunch(b->gexec, b->st));
+    b->graph_launches += nsteps;
+  } else {
+    for (int i = 0; i < nsteps; ++i) AFE_TRY(enqueue_step(b->plan, dt));
+  }
+  b->launches += (int64_t)per * nsteps;
+  b->pending += nsteps;
+  return AFE_OK;
+}
+
+afe_status afe_batch_sync(afe_batch* b, int* member_status) {
+  if (!b) return fail(AFE_EINVAL, "NULL batch");
+  const int nh = b->bt.nh;
+  std::vector<int> flags((size_t)nh * afe::F_COUNT);
+  std::vector<double> dts(nh), ts(nh);
+  for (int h = 0; h < nh; ++h) {
+    const afe::DevMesh& d = b->bt.tab[h];
+    AFE_CUDA(cudaMemcpyAsync(&flags[(size_t)h * afe::F_COUNT], d.flags, afe::F_COUNT * sizeof(int),
+                             cudaMemcpyDeviceToHost, b->st));
+    AFE_CUDA(cudaMemcpyAsync(&dts[h], d.dt, sizeof(double), cudaMemcpyDeviceToHost, b->st));
+    AFE_CUDA(cudaMemcpyAsync(&ts[h], d.tacc, sizeof(double), cudaMemcpyDeviceToHost, b->st));
+  }
+  AFE_CUDA(cudaStreamSynchronize(b->st));
+  afe_status worst = AFE_OK;
+  std::string first_msg;
+  for (int h = 0; h < nh; ++h) {
+    afe_mesh* m = b->mem[h];
+    m->last_dt = dts[h];
+    m->t_host = ts[h];
+    m->steps += b->pending;
+    m->pending = 0;
+    const afe_status s = status_of(&flags[(size_t)h * afe::F_COUNT]);
+    if (member_status) member_status[h] = (int)s;
+    if (s != AFE_OK && (worst == AFE_OK || (int)s > (int)worst)) {
+      worst = s;
+      first_msg = "member " + std::to_string(h) + ": " + g_err;
+    }
+  }
+  b->pending = 0;
+  if (worst != AFE_OK) return fail(worst, first_msg);
+  return AFE_OK;
+}
+
+afe_status afe_batch_info(const afe_batch* b, int64_t* n_cells, int64_t* n_nodes, int64_t* launches,
+                          int64_t* graph_launches) {
+  if (!b) return fail(AFE_EINVAL, "NULL batch");
+  if (n_cells) *n_cells = b->bt.cpre[b->bt.nh];
+  if (n_nodes) {
+    int64_t n = 0;
+    for (afe_mesh* m : b->mem) n += m->topo.n_nodes;
+    *n_nodes = n;
+  }
+  if (launches) *launches = b->launches;
+  if (graph_launches) *graph_launches = b->graph_launches;
+  return AFE_OK;
+}
+
+void afe_batch_destroy(afe_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  delete b;
 }
 
 }  // extern "C"

@@ -74,6 +74,32 @@ struct DevMesh {
   int picard_max, limiter, eq;
 };
 
+// A set of meshes stepped by one launch per stage (one mesh is a batch of one).  The whole
+// table travels as one __grid_constant__ kernel parameter (about 31 KB, below the 32 KB
+// parameter limit), so every field read stays a constant-bank load as with a single DevMesh
+// passed by value, and a captured graph node carries its own copy of the table.
+constexpr int kMaxBatch = 64;
+struct Batch {
+  int nh;                        // members in use
+  int Nmax, Smax;                // maxima over the members (shared-memory layout)
+  int pad;
+  int* work;                     // work counter of the persistent predictor
+  int64_t cpre[kMaxBatch + 1];   // prefix sums of the members' cells
+  int64_t gpre[kMaxBatch + 1];   // prefix sums of the members' polygonal faces
+  DevMesh tab[kMaxBatch];
+};
+
+// Member holding global item x of a prefix-sum array (largest h with pre[h] <= x).
+__device__ __forceinline__ int batch_find(const int64_t* __restrict__ pre, int nh, int64_t x) {
+  int lo = 0, hi = nh - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ double cell_kappa(const DevMesh& m, double mu_i) {
   return m.kappa0 >= 0.0 ? m.kappa0 : mu_i * m.gamma * m.cv / m.Pr;
 }
@@ -319,10 +345,33 @@ __global__ void symmetrize_kernel(DevMesh m, int make32) {
 }
 
 // ----------------------------------------------------------------------------------------
-// Sec. 4.5: cell means u_bar_i = w_i . u_i / |P_i|  (w_i = M_i 1), one block per cell.
-__global__ void cell_means_kernel(DevMesh m) {
+// Per-step kernels over a batch of meshes (one mesh is a batch of one).
+//
+// Start of a series of steps: clear every member's status flags (they then accumulate over
+// the steps until the host reads them).
+__global__ void flags_clear_kernel(const __grid_constant__ Batch bt) {
+  for (int h = threadIdx.x; h < bt.nh; h += blockDim.x) {
+#pragma unroll
+    for (int f = 0; f < F_COUNT; ++f) bt.tab[h].flags[f] = 0;
+  }
+}
+
+// Start of a step: clear every member's CFL maximum and the shared work counter of the
+// persistent predictor.
+__global__ void step_begin_kernel(const __grid_constant__ Batch bt) {
+  for (int h = threadIdx.x; h < bt.nh; h += blockDim.x) *bt.tab[h].maxbits = 0ull;
+  if (threadIdx.x == 0) *bt.work = 0;
+}
+
+// Sec. 4.5: cell means u_bar_i = w_i . u_i / |P_i|  (w_i = M_i 1), one block per cell at a time.
+__global__ void cell_means_kernel(const __grid_constant__ Batch bt) {
   __shared__ double sh[5][256];
-  for (int64_t c = blockIdx.x; c < m.C; c += gridDim.x) {
+  const int64_t total = bt.cpre[bt.nh];
+  for (int64_t gc = blockIdx.x; gc < total; gc += gridDim.x) {
+    const int hh = batch_find(bt.cpre, bt.nh, gc);
+    const DevMesh& m = bt.tab[hh];
+    if (!m.limiter) continue;  // block-uniform
+    const int64_t c = gc - bt.cpre[hh];
     const int64_t n0 = m.node_ptr[c], n1 = m.node_ptr[c + 1];
     double acc[5] = {0, 0, 0, 0, 0};
     for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
@@ -344,12 +393,15 @@ __global__ void cell_means_kernel(DevMesh m) {
   }
 }
 
-// Flattener beta_i (Eq. beta3D) and mu_i = mu + beta_i rho_i |lambda|_i h_i/(2N+1); one
-// thread per cell.  div v_i from face-neighbour cell-mean velocities, c_min over the cell and
-// its neighbours; domain-boundary faces add nothing.
-__global__ void limiter_kernel(DevMesh m) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= m.C) return;
+// Artificial-viscosity limiter (Sec. 4.5, Eq. beta3D): beta_i from the discrete velocity
+// divergence of the cell means over the faces of P_i, mu_i = mu + beta_i rho_i lambda_i h_i/(2N+1).
+__global__ void limiter_kernel(const __grid_constant__ Batch bt) {
+  const int64_t gc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gc >= bt.cpre[bt.nh]) return;
+  const int hh = batch_find(bt.cpre, bt.nh, gc);
+  const DevMesh& m = bt.tab[hh];
+  if (!m.limiter) return;  // a batch member without the limiter keeps beta = 0, mu_i = mu
+  const int64_t c = gc - bt.cpre[hh];
   auto prim = [&](int64_t i, double v[3], double& rho, double& cs) {
     const double* q = m.means + i * 5;
     rho = q[0];
@@ -377,42 +429,57 @@ __global__ void limiter_kernel(DevMesh m) {
   if (b > 0.0) atomicAdd(&m.flags[F_TROUBLED], 1);
 }
 
-// Sec. 4.2: max over all nodes of |lambda| + 2 |lambda^v| (2N+1)/h_i; positive doubles
-// order like their bit patterns, so the max is an integer atomic (order independent).
-__global__ void cfl_kernel(DevMesh m) {
-  __shared__ double sh[64];
-  double best = 0.0, dummy = 0.0;
-  for (int64_t c = blockIdx.x; c < m.C; c += gridDim.x) {
-    const double mu_i = m.mu[c], kap = cell_kappa(m, mu_i), h = m.cell_h[c];
-    for (int64_t n = m.node_ptr[c] + threadIdx.x; n < m.node_ptr[c + 1]; n += blockDim.x) {
-      const double* q = m.u + n * 5;
-      const double rho = q[0];
-      const double v0 = q[1] / rho, v1 = q[2] / rho, v2 = q[3] / rho;
-      const double p = (m.gamma - 1.0) * (q[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
-      const double lam = sqrt(v0 * v0 + v1 * v1 + v2 * v2) + sqrt(m.gamma * p / rho);
-      const double lv = fmax(4.0 * mu_i / (3.0 * rho), kap / (m.cv * rho));
-      double br = lam + 2.0 * lv * (2 * m.N + 1) / h;
-      if (!(br >= 0.0) || !isfinite(br)) {  // inadmissible state: report and keep dt finite
-        atomicOr(&m.flags[F_NONFINITE], 1);
-        br = 0.0;
-      }
-      best = fmax(best, br);
+// CFL bound (Sec. 4.6): max over nodes of lambda + 2 lambda_v (2N+1)/h_i, one warp per cell,
+// folded into the member's maximum by an integer atomicMax on the bits of a non-negative
+// double (order-independent, hence deterministic).
+__global__ void cfl_kernel(const __grid_constant__ Batch bt) {
+  const int64_t gc = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gc >= bt.cpre[bt.nh]) return;
+  const int hh = batch_find(bt.cpre, bt.nh, gc);
+  const DevMesh& m = bt.tab[hh];
+  const int64_t c = gc - bt.cpre[hh];
+  const double mu_i = m.mu[c], kap = cell_kappa(m, mu_i), h = m.cell_h[c];
+  double best = 0.0;
+  bool bad = false;
+  for (int64_t n = m.node_ptr[c] + lane; n < m.node_ptr[c + 1]; n += 32) {
+    const double* q = m.u + n * 5;
+    const double rho = q[0];
+    const double v0 = q[1] / rho, v1 = q[2] / rho, v2 = q[3] / rho;
+    const double p = (m.gamma - 1.0) * (q[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
+    const double lam = sqrt(v0 * v0 + v1 * v1 + v2 * v2) + sqrt(m.gamma * p / rho);
+    const double lv = fmax(4.0 * mu_i / (3.0 * rho), kap / (m.cv * rho));
+    double br = lam + 2.0 * lv * (2 * m.N + 1) / h;
+    if (!(br >= 0.0) || !isfinite(br)) {  // inadmissible state: report and keep dt finite
+      bad = true;
+      br = 0.0;
     }
+    best = fmax(best, br);
   }
-  block_max2(best, dummy, sh);
-  if (threadIdx.x == 0) atomicMax(m.maxbits, (unsigned long long)__double_as_longlong(best));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&m.flags[F_NONFINITE], 1);
+  if (lane == 0) atomicMax(m.maxbits, (unsigned long long)__double_as_longlong(best));
 }
 
-__global__ void dt_finalize_kernel(DevMesh m) {
-  const double mx = __longlong_as_double((long long)*m.maxbits);
-  double dt = mx > 0.0 ? m.cfl * m.h_min / ((2 * m.N + 1) * mx) : 0.0;
-  if (!(dt > 0.0)) atomicOr(&m.flags[F_NONFINITE], 4);
-  *m.dt = dt;
+// dt = CFL h_min / ((2N+1) max_bound) per member (Sec. 4.6)
+__global__ void dt_finalize_kernel(const __grid_constant__ Batch bt) {
+  for (int h = threadIdx.x; h < bt.nh; h += blockDim.x) {
+    const DevMesh& m = bt.tab[h];
+    const double mx = __longlong_as_double((long long)*m.maxbits);
+    double dt = mx > 0.0 ? m.cfl * m.h_min / ((2 * m.N + 1) * mx) : 0.0;
+    if (!(dt > 0.0)) atomicOr(&m.flags[F_NONFINITE], 4);
+    *m.dt = dt;
+  }
 }
 
-__global__ void set_dt_kernel(DevMesh m, double dt) { *m.dt = dt; }
+__global__ void set_dt_kernel(const __grid_constant__ Batch bt, double dt) {
+  for (int h = threadIdx.x; h < bt.nh; h += blockDim.x) *bt.tab[h].dt = dt;
+}
 
-__global__ void advance_time_kernel(DevMesh m) { *m.tacc += *m.dt; }
+__global__ void advance_time_kernel(const __grid_constant__ Batch bt) {
+  for (int h = threadIdx.x; h < bt.nh; h += blockDim.x) *bt.tab[h].tacc += *bt.tab[h].dt;
+}
 
 // ----------------------------------------------------------------------------------------
 // Space-time predictor (Sec. 4.3).  Persistent: each block takes cells from a work
@@ -723,11 +790,14 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
 // sub-triangles, both sides).  The wave speeds are reduced over the face with warp
 // shuffles; G is written for the own side and, negated, for the matched side.
 template <int N, typename Real>
-__global__ void face_kernel(DevMesh m) {
+__global__ void face_kernel(const __grid_constant__ Batch bt) {
   constexpr int NF = nf_of(N);
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t ggw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (gw >= m.n_groups) return;
+  if (ggw >= bt.gpre[bt.nh]) return;
+  const int h = batch_find(bt.gpre, bt.nh, ggw);
+  const DevMesh& m = bt.tab[h];
+  const int64_t gw = ggw - bt.gpre[h];
   const int64_t g0 = m.group_ptr[gw], g1 = m.group_ptr[gw + 1];
   const int nitems = (int)(g1 - g0) * NF;
   const Real* sq = (const Real*)m.slot_q;

@@ -156,7 +156,8 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
 }
 
 template <int N>
-__global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m, const RefData* __restrict__ ref,
+__global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __grid_constant__ Batch bt,
+                                                                        const RefData* __restrict__ ref,
                                                                         int diag, int smem_bytes) {
   constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), NC = NT * 5, SR = f32_row_stride(N);
   constexpr int NPP = (NP + 3) / 4 * 4;  // rows of sSt padded to 16 bytes
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
   __shared__ int64_t sCell;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int Nmax = m.Nmax;
+  const int Nmax = bt.Nmax;
   auto up = [](size_t x) { return (x + 127) / 128 * 128; };
   unsigned char* p = smem_raw;
   float* sR = (float*)p;    // [CH][NT][NP][5]
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
   float* sBw = (float*)p;   // [warps][3][NP][5]
   p += up((size_t)kF32Warps * 3 * NP * 5 * 4);
   unsigned char* srec = p;  // [S][REC] sub-tet records of the current cell
-  p += up((size_t)m.Smax * REC);
+  p += up((size_t)bt.Smax * REC);
   unsigned char* const cell_base = p;  // per cell: sq [Ni][SR], srhs [Ni][SR], M_i^-1 ring
   float* sB = sBw + warp * 3 * NP * 5;
   (void)Nmax;
@@ -212,17 +213,21 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(DevMesh m
   __syncthreads();
   uint32_t phase = 0;
   uint32_t fpar = 0, epar = 0;  // parities of the next completion of sfull[s] / sempty[s]
-  const float dt = (float)*m.dt;
-  const float gam = (float)m.gamma, Rg = (float)m.Rgas;
-  const float tol = (float)m.tol;
+  const int64_t total = bt.cpre[bt.nh];
   auto rec_g = [&](int k) { return reinterpret_cast<const float*>(srec + (size_t)k * REC); };
   auto rec_a = [&](int k) { return reinterpret_cast<const uint16_t*>(srec + (size_t)k * REC + 40); };
 
   for (;;) {
-    if (tid == 0) sCell = atomicAdd(m.work, 1);
+    if (tid == 0) sCell = atomicAdd(bt.work, 1);
     __syncthreads();
-    const int64_t c = sCell;
-    if (c >= m.C) break;
+    const int64_t gc = sCell;
+    if (gc >= total) break;
+    const int h = batch_find(bt.cpre, bt.nh, gc);
+    const DevMesh& m = bt.tab[h];
+    const int64_t c = gc - bt.cpre[h];
+    const float dt = (float)*m.dt;
+    const float gam = (float)m.gamma, Rg = (float)m.Rgas;
+    const float tol = (float)m.tol;
     const int64_t n0 = m.node_ptr[c];
     const int Ni = (int)(m.node_ptr[c + 1] - n0);
     const int LD = minv_ld(Ni);
@@ -717,7 +722,8 @@ namespace afe {
 constexpr int kCorrThreads = 128;
 
 template <int N>
-__global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(DevMesh m, const RefData* __restrict__ ref) {
+__global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __grid_constant__ Batch bt,
+                                                                        const RefData* __restrict__ ref) {
   constexpr int NF = nf_of(N);
   extern __shared__ __align__(16) float sr[];  // [Nmax][5]
   __shared__ float sZ[NF][NF];
@@ -731,8 +737,11 @@ __global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(DevMesh m, 
     szs[tid] = z;
   }
   __syncthreads();
-  const int64_t c = blockIdx.x;
-  if (c >= m.C) return;
+  const int64_t gc = blockIdx.x;
+  if (gc >= bt.cpre[bt.nh]) return;
+  const int h = batch_find(bt.cpre, bt.nh, gc);
+  const DevMesh& m = bt.tab[h];
+  const int64_t c = gc - bt.cpre[h];
   const int64_t n0 = m.node_ptr[c];
   const int Ni = (int)(m.node_ptr[c + 1] - n0);
   const int LD = minv_ld(Ni);

@@ -1,0 +1,282 @@
+"""Continuous batching of many independent ADER-AFE simulations on one GPU.
+
+A request asks for ``nsteps`` CFL steps of one simulation: a mesh from a catalogue of
+resident meshes and an initial state.  Meshes are set up once (topology, mass matrices and
+their inverses: the costly part), as a pool of *slots* -- mesh handles whose state buffers
+are reused by successive requests, sized up front to a device-memory budget.  The server
+loop admits arrived requests into free slots of their mesh, advances every occupied slot
+together with one launch per stage (``afe_batch_step_async``: the kernels take a table of
+meshes, so a batch of small meshes fills the GPU as one large mesh does), and retires
+requests as they finish, so that new requests join a running batch at the next step
+boundary instead of waiting for the whole batch to drain.
+
+The GPU engine is a thin layer over the C ABI; every step of the computation runs in the
+library's kernels.  The scheduling logic is independent of it (any object with the
+engine's methods will do), which keeps it testable without a GPU.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import OrderedDict, deque
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import afe as _afe
+
+
+@dataclass
+class Request:
+    rid: int
+    mesh: str                       # catalogue key
+    nsteps: int                     # CFL steps to take
+    arrival: float                  # seconds after the start of the run
+    q0: Optional[np.ndarray] = None # initial state [n_nodes, 5]; None: the engine's default
+    # filled in by the server
+    admitted: float = math.nan
+    done: float = math.nan
+    status: int = 0
+    q: Optional[np.ndarray] = None  # final state (when the server keeps results)
+    t: float = math.nan             # simulated time reached
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+@dataclass
+class Slot:
+    sid: int
+    mesh: str
+    handle: object
+    n_nodes: int
+    nbytes: int
+    busy: Optional[Request] = None
+    remaining: int = 0
+
+
+class GpuEngine:
+    """Slot pool on the current CUDA device.
+
+    catalogue: key -> object with the arrays of ``afe_mesh_create`` (``xyz``,
+    ``cell_subtet_ptr``, ``subtet_vtx``, ``subtet_shift``, ``periodic``, ``period``).
+    slots: key -> number of slots of that mesh.  params: FP32 ``afe_params`` shared by the
+    slots.  default_state: key -> [n_nodes, 5] state used when a request brings none.
+    budget_bytes: the pool may not exceed this much device memory (None: no limit).
+    """
+
+    def __init__(self, catalogue, slots: Dict[str, int], params, default_state=None, budget_bytes=None,
+                 stream: int = 0, use_graph: bool = True, max_cached_batches: int = 16):
+        if params.precision != _afe.AFE_FP32:
+            raise ValueError("batched stepping needs AFE_FP32 parameters")
+        self.params = params
+        self.stream = stream
+        self.use_graph = use_graph
+        self.slots: List[Slot] = []
+        self.default_state = dict(default_state or {})
+        self._batches: "OrderedDict[tuple, object]" = OrderedDict()
+        self._max_cached = max_cached_batches
+        total = 0
+        for key, count in slots.items():
+            pm = catalogue[key]
+            for _ in range(count):
+                h = _afe.create_from_polymesh(pm, params, stream)
+                nb = _afe.afe_device_bytes(h)
+                if budget_bytes is not None and total + nb > budget_bytes:
+                    _afe.afe_mesh_destroy(h)
+                    break
+                total += nb
+                self.slots.append(Slot(len(self.slots), key, h, _afe.afe_num_nodes(h), nb))
+        self.device_bytes = total
+
+    # -- engine interface used by the server
+    def load(self, slot: Slot, q0):
+        q = self.default_state[slot.mesh] if q0 is None else q0
+        _afe.afe_set_state(slot.handle, q)
+
+    def step(self, slots: Sequence[Slot], nsteps: int) -> List[int]:
+        key = tuple(s.sid for s in slots)
+        b = self._batches.pop(key, None)
+        if b is None:
+            b = _afe.afe_batch_create([s.handle for s in slots], self.stream)
+            while len(self._batches) >= self._max_cached:
+                _, old = self._batches.popitem(last=False)
+                _afe.afe_batch_destroy(old)
+        self._batches[key] = b
+        _afe.afe_batch_step_async(b, 0.0, nsteps, self.use_graph)
+        _, ms = _afe.afe_batch_sync(b, len(slots), check=False)
+        return [int(x) for x in ms]
+
+    def step_alone(self, slot: Slot, nsteps: int) -> int:
+        _afe.afe_step_async(slot.handle, 0.0, nsteps)
+        return _afe.afe_sync(slot.handle, check=False)
+
+    def read(self, slot: Slot):
+        return _afe.afe_get_state(slot.handle), _afe.afe_get_stats(slot.handle).t
+
+    def close(self):
+        for b in self._batches.values():
+            _afe.afe_batch_destroy(b)
+        self._batches.clear()
+        for s in self.slots:
+            _afe.afe_mesh_destroy(s.handle)
+        self.slots = []
+
+
+@dataclass
+class RunStats:
+    requests: int
+    makespan_s: float
+    dof_updates: float
+    throughput: float               # DOF-updates per second over the run
+    p50_s: float
+    p99_s: float
+    mean_s: float
+    steps_launched: int             # batch steps (or single steps) issued
+    mean_batch: float               # mean members per batch step
+    failed: int
+    latencies: List[float] = field(default_factory=list)
+
+    def as_dict(self):
+        d = dict(self.__dict__)
+        d.pop("latencies")
+        return d
+
+
+class Server:
+    """Continuous-batching loop over an engine's slots.
+
+    mode "batch": all occupied slots advance together, ``chunk`` steps per iteration with
+    chunk = min(max_chunk, fewest steps any running request still needs), so no request is
+    stepped past its nsteps and a finished slot is refilled at the next iteration.
+    mode "serial": one request at a time, alone (the unbatched baseline).
+    Admission is first come, first served per mesh: a request waits until a slot of its mesh
+    is free; requests for other meshes may pass it.
+    """
+
+    def __init__(self, engine, mode: str = "batch", max_chunk: int = 4, keep_results: bool = False,
+                 clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep):
+        if mode not in ("batch", "serial"):
+            raise ValueError("mode is 'batch' or 'serial'")
+        self.engine = engine
+        self.mode = mode
+        self.max_chunk = max(1, int(max_chunk))
+        self.keep_results = keep_results
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests: Sequence[Request]) -> RunStats:
+        pending = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        waiting: Dict[str, deque] = {}
+        slots = self.engine.slots
+        mesh_keys = {s.mesh for s in slots}
+        for r in pending:
+            if r.mesh not in mesh_keys:
+                raise ValueError(f"request {r.rid}: no slot holds mesh {r.mesh!r}")
+        t0 = self.clock()
+        now = lambda: self.clock() - t0  # noqa: E731
+        finished: List[Request] = []
+        steps_launched = 0
+        members_total = 0
+        dof_updates = 0.0
+        n_total = len(pending)
+        while len(finished) < n_total:
+            # arrivals
+            tnow = now()
+            while pending and pending[0].arrival <= tnow:
+                r = pending.popleft()
+                waiting.setdefault(r.mesh, deque()).append(r)
+            # admission
+            free_by_mesh: Dict[str, List[Slot]] = {}
+            for s in slots:
+                if s.busy is None:
+                    free_by_mesh.setdefault(s.mesh, []).append(s)
+            if self.mode == "serial":
+                running = [s for s in slots if s.busy is not None]
+                if not running:
+                    # the oldest waiting request of any mesh
+                    cands = [(q[0].arrival, q[0].rid, k) for k, q in waiting.items() if q and free_by_mesh.get(k)]
+                    if cands:
+                        _, _, k = min(cands)
+                        self._admit(waiting[k].popleft(), free_by_mesh[k][0], tnow)
+            else:
+                for k, q in waiting.items():
+                    free = free_by_mesh.get(k, [])
+                    while q and free:
+                        self._admit(q.popleft(), free.pop(0), tnow)
+            running = [s for s in slots if s.busy is not None]
+            if not running:
+                if pending:
+                    dt = pending[0].arrival - now()
+                    if dt > 0:
+                        self.sleep(dt)
+                    continue
+                raise RuntimeError("requests left waiting with no slot able to take them")
+            # advance
+            if self.mode == "serial":
+                s = running[0]
+                chunk = s.remaining
+                statuses = [self.engine.step_alone(s, chunk)]
+            else:
+                chunk = min(self.max_chunk, min(s.remaining for s in running))
+                statuses = self.engine.step(running, chunk)
+            steps_launched += chunk
+            members_total += chunk * len(running)
+            tdone = now()
+            for s, st in zip(running, statuses):
+                s.remaining -= chunk
+                dof_updates += 5.0 * s.n_nodes * chunk
+                if st != 0 and s.busy.status == 0:
+                    s.busy.status = st
+                if s.remaining == 0:
+                    r = s.busy
+                    if self.keep_results:
+                        r.q, r.t = self.engine.read(s)
+                    r.done = tdone
+                    finished.append(r)
+                    s.busy = None
+        makespan = now()
+        lat = sorted(r.latency for r in finished)
+        return RunStats(
+            requests=n_total,
+            makespan_s=makespan,
+            dof_updates=dof_updates,
+            throughput=dof_updates / makespan if makespan > 0 else math.nan,
+            p50_s=_quantile(lat, 0.50),
+            p99_s=_quantile(lat, 0.99),
+            mean_s=float(np.mean(lat)) if lat else math.nan,
+            steps_launched=steps_launched,
+            mean_batch=members_total / steps_launched if steps_launched else 0.0,
+            failed=sum(1 for r in finished if r.status != 0),
+            latencies=lat,
+        )
+
+    def _admit(self, r: Request, s: Slot, tnow: float):
+        self.engine.load(s, r.q0)
+        s.busy = r
+        s.remaining = int(r.nsteps)
+        r.admitted = tnow
+
+
+def _quantile(sorted_vals: Sequence[float], q: float) -> float:
+    """Nearest-rank quantile of sorted values."""
+    if not sorted_vals:
+        return math.nan
+    k = max(0, min(len(sorted_vals) - 1, int(math.ceil(q * len(sorted_vals))) - 1))
+    return float(sorted_vals[k])
+
+
+def poisson_requests(rate_per_s: float, n: int, meshes: Sequence[str], nsteps: Sequence[int], seed: int = 0,
+                     weights: Optional[Sequence[float]] = None) -> List[Request]:
+    """n requests with exponential inter-arrival times (a Poisson process of the given
+    rate), each for a mesh and a step count drawn uniformly (or with ``weights``)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_per_s) if rate_per_s > 0 else 0.0
+        k = rng.choice(len(meshes), p=None if weights is None else np.asarray(weights) / np.sum(weights))
+        out.append(Request(rid=i, mesh=meshes[k], nsteps=int(rng.choice(nsteps)), arrival=t))
+    return out

@@ -1,0 +1,144 @@
+"""Batched stepping on the GPU: several meshes advanced by one launch per stage give, for
+every member, exactly (bit for bit) the result of stepping that member alone -- with and
+without the captured CUDA graph, in any mix of meshes, equations and limiter settings, and
+through the continuous-batching server where a request's batch changes under it."""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import states
+from inputs.voronoi import box_voronoi, periodic_voronoi
+
+pytestmark = pytest.mark.gpu
+
+K = 5
+
+
+@pytest.fixture(scope="module")
+def afe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2605_00619_gb300 import afe as mod
+    mod.lib()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def meshes():
+    return {"a": periodic_voronoi(3), "b": box_voronoi(3, seed=2), "c": periodic_voronoi(4, seed=1)}
+
+
+def _members(afe, meshes, order=2):
+    """(handle, initial state) of four members: Euler density wave, a limited explosion on a
+    box, Navier-Stokes Taylor-Green, and a second handle of the first mesh at rest."""
+    fp32 = dict(precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+    specs = [
+        ("a", afe.afe_default_params(order, **fp32), states.density_wave),
+        ("b", afe.afe_default_params(order, limiter=1, **fp32), lambda x: states.spherical_riemann(x, alpha0=0.3)),
+        ("c", afe.afe_default_params(order, equations=afe.AFE_NAVIER_STOKES, mu=0.005, kappa=-1.0, Pr=0.71, **fp32),
+         lambda x: states.taylor_green_3d(2 * math.pi * x, p0=10.0)),
+        ("a", afe.afe_default_params(order, **fp32), states.constant),
+    ]
+    out = []
+    for key, p, ic in specs:
+        h = afe.create_from_polymesh(meshes[key], p)
+        out.append((h, ic(afe.afe_get_node_coords(h))))
+    return out
+
+
+def _alone(afe, members, nsteps):
+    res = []
+    for h, u0 in members:
+        afe.afe_set_state(h, u0)
+        afe.afe_step_async(h, 0.0, nsteps)
+        st = afe.afe_sync(h, check=False)
+        res.append((afe.afe_get_state(h), afe.afe_get_stats(h).dt, st))
+    return res
+
+
+def _batched(afe, members, splits, use_graph):
+    for h, u0 in members:
+        afe.afe_set_state(h, u0)
+    b = afe.afe_batch_create([h for h, _ in members])
+    worst = np.zeros(len(members), np.int32)
+    for n in splits:
+        afe.afe_batch_step_async(b, 0.0, n, use_graph)
+        _, ms = afe.afe_batch_sync(b, len(members), check=False)
+        worst = np.maximum(worst, ms)
+    info = afe.afe_batch_info(b)
+    afe.afe_batch_destroy(b)
+    return [(afe.afe_get_state(h), afe.afe_get_stats(h).dt) for h, _ in members], worst, info
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_alone_bitwise(afe, meshes, use_graph):
+    mem = _members(afe, meshes)
+    ref = _alone(afe, mem, K)
+    got, statuses, info = _batched(afe, mem, [2, K - 2], use_graph)
+    for i, ((qa, dta, sta), (qb, dtb)) in enumerate(zip(ref, got)):
+        np.testing.assert_array_equal(qb, qa, err_msg=f"member {i}")
+        assert dta == dtb
+        assert sta in (0, 5) and statuses[i] == sta
+        assert np.isfinite(qb).all()
+    cells = sum(m.n_cells for m in (meshes["a"], meshes["b"], meshes["c"], meshes["a"]))
+    assert info[0] == cells
+    assert info[2] > 0 and (info[3] == K) == use_graph
+    for h, _ in mem:
+        afe.afe_mesh_destroy(h)
+
+
+def test_batch_of_one_and_member_order(afe, meshes):
+    mem = _members(afe, meshes)
+    ref = _alone(afe, mem, 3)
+    got, _, _ = _batched(afe, mem[:1], [3], True)
+    np.testing.assert_array_equal(got[0][0], ref[0][0])
+    rev = mem[::-1]
+    got, _, _ = _batched(afe, rev, [1, 1, 1], True)
+    for (qa, _, _), (qb, _) in zip(ref[::-1], got):
+        np.testing.assert_array_equal(qb, qa)
+    for h, _ in mem:
+        afe.afe_mesh_destroy(h)
+
+
+def test_batch_rejects_unsupported_members(afe, meshes):
+    pm = meshes["a"]
+    h32 = afe.create_from_polymesh(pm, afe.afe_default_params(2, precision=afe.AFE_FP32))
+    h64 = afe.create_from_polymesh(pm, afe.afe_default_params(2))
+    h3 = afe.create_from_polymesh(pm, afe.afe_default_params(3, precision=afe.AFE_FP32))
+    for members in ([h32, h64], [h32, h3], [h32, h32], []):
+        b, st = afe.afe_batch_create(members, check=False)
+        assert b is None and st == afe.AFE_EINVAL
+    for h in (h32, h64, h3):
+        afe.afe_mesh_destroy(h)
+
+
+def test_serving_loop_results_equal_alone(afe, meshes):
+    from paper_2605_00619_gb300.serving import GpuEngine, Request, Server
+    p = afe.afe_default_params(2, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+    cat = {"a": meshes["a"], "c": meshes["c"]}
+    eng = GpuEngine(cat, {"a": 2, "c": 2}, p)
+    ics = {"a": states.density_wave, "c": lambda x: states.constant(x, vel=(0.1, 0.2, 0.3))}
+    for s in eng.slots:
+        eng.default_state.setdefault(s.mesh, ics[s.mesh](afe.afe_get_node_coords(s.handle)))
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(9):
+        key = "a" if i % 3 else "c"
+        u0 = eng.default_state[key] * (1.0 + 0.01 * rng.random())
+        reqs.append(Request(i, key, int(rng.integers(1, 6)), 0.0, q0=u0))
+    stats = Server(eng, max_chunk=2, keep_results=True).run(reqs)
+    assert stats.requests == 9 and stats.failed == 0
+    assert stats.mean_batch > 1.0
+    # the same requests one by one on fresh handles
+    solo = {k: afe.create_from_polymesh(pm, p) for k, pm in cat.items()}
+    for r in reqs:
+        h = solo[r.mesh]
+        afe.afe_set_state(h, r.q0)
+        afe.afe_step_async(h, 0.0, r.nsteps)
+        assert afe.afe_sync(h, check=False) == 0
+        np.testing.assert_array_equal(r.q, afe.afe_get_state(h), err_msg=f"request {r.rid}")
+    for h in solo.values():
+        afe.afe_mesh_destroy(h)
+    eng.close()
