@@ -3,20 +3,23 @@
 // One block of 512 threads per cell (persistent: blocks take cells from a work counter).
 // The cell's working set stays in shared memory for the whole fixed-point iteration:
 //   sq   [N_i][Nt*5|1]  space-time nodal coefficients q (node-major, odd row stride)
-//   srhs [N_i][Nt*5|1]  right-hand side sum_k A_k^T R_k, then Y, then the volume term
+//   srhs [N_i][5][NTP]  right-hand side sum_k A_k^T R_k, then Y (time slices padded to a
+//                       vector width NTP: one vector load per (row, variable))
 //   sR   [CH][Nt][Np][5]  per-chunk sub-tet results R_{k,t} (deterministic gather buffer)
-//   sB   [warps][3][Np][5]  per-warp flux pre-contraction of one (sub-tet, time)
+//   sB   [CH][3 Np][5][NTP]  pre-contracted fluxes of the chunk's sub-tets (time innermost)
 //   sM   [NSTAGE][rows][LD] pipelined stages of M_i^-1
 // Per iteration:
-//   1. for chunks of CH sub-tets: every warp takes (sub-tet k, time t) pairs; lanes j < Np
-//      evaluate the flux at node j and pre-contract it with dt adj(J_k) (f*, g*, h*); lanes
-//      (m, v) then form R[m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v] in 4-row tiles; after
-//      the chunk each thread adds, in registers for the nodes it owns, the chunk's incidences
-//      in (k, j) order (fixed order: the sum is bitwise reproducible and has no atomics);
+//   1. for chunks of CH sub-tets: every thread takes (sub-tet k, node j, time t) items,
+//      evaluates the flux and pre-contracts it with dt adj(J_k) (f*, g*, h*) into B; then
+//      every thread takes a (k, v, time pair, 4 rows m) tile of the reference-stiffness
+//      contraction R[t][m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v][t] (one float4 of S^ and
+//      one float2 of B per 8 FMAs); after the chunk each thread adds, in registers for the
+//      nodes it owns, the chunk's incidences in (k, j) order (fixed order: the sum is
+//      bitwise reproducible and has no atomics);
 //   2. Y = M_i^-1 RHS with M_i^-1 streamed through shared memory in stages of `rows` rows by
-//      cp.async.bulk (TMA bulk copies, completion on an mbarrier); thread (row group, time
-//      slice) keeps 4 x 5 tiles of Y in registers (M_i^-1 is symmetric: row l of the stage
-//      serves column l);
+//      cp.async.bulk (TMA bulk copies, completion on an mbarrier); thread (row group,
+//      variable) keeps 4 x NTP tiles of Y in registers and reads one vector of M_i^-1 and one
+//      of RHS per row of the stage (M_i^-1 is symmetric: row l of the stage serves column l);
 //      q^{r+1}[n,s] = u^[n] - sum_t K1t^-1[s,t] Y[n,t] and the residual, in registers.
 // Epilogue: vol = sum_k A_k^T sum_d S^_d^T adj(J_k) F_bar_k, and q_bar, F_bar . n on the face
 // slots, as the FP64 kernel.  Every mbarrier wait is bounded; a wait that runs out sets
@@ -24,6 +27,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -31,7 +35,6 @@ namespace afe {
 
 constexpr int kF32Threads = 512;
 constexpr int kF32Warps = kF32Threads / 32;
-constexpr int kF32Chunk = 16;    // sub-tets per gather chunk
 constexpr int kF32Rows = 16;     // rows of M_i^-1 per pipeline stage
 constexpr int kF32MaxStages = 8;
 constexpr int kF32Consumers = kF32Warps - 1;  // warps that apply M_i^-1 (the last one loads it)
@@ -86,13 +89,19 @@ constexpr int kF32MaxNodes = 640;
 constexpr int kF32Items = 5;  // ceil(640 * 4 / 512)
 inline int predictor_f32_max_nodes(int N) {
   const int by_items = kF32Items * kF32Threads / (N + 1);
-  const int by_rows = 8 * (kF32Consumers * 32 / (N + 1));
+  const int by_rows = 8 * (kF32Consumers * 32 / 5);
+  (void)N;
   return std::min(kF32MaxNodes, std::min(by_items, by_rows));
 }
 
-// Row stride (floats) of the per-node arrays in shared memory: Nt*5 made odd, so that one
-// thread per row touches 32 different banks.
+// Row stride (floats) of q in shared memory: Nt*5 made odd, so that one thread per row
+// touches 32 different banks.
 constexpr int f32_row_stride(int N) { return ((N + 1) * 5) | 1; }
+// Time slices of RHS / Y padded to a vector width, and their row stride [5][NTP].
+constexpr int f32_ntp(int N) { return N == 1 ? 2 : 4; }
+constexpr int f32_rhs_stride(int N) { return 5 * f32_ntp(N); }
+// Sub-tets per chunk of the right-hand side (16 time-slice pairs of B per chunk).
+constexpr int f32_chunk(int N) { return f32_ntp(N) == 4 ? 8 : 16; }
 
 // Packed FP32 sub-tet record: adj(J) row-major (9 floats), det J, then the Np cell-local node
 // ids (uint16); padded to 16 bytes so that a cell's records are one bulk copy.
@@ -101,16 +110,21 @@ constexpr int f32_rec_bytes(int N) { return (40 + 2 * np_of(N) + 15) / 16 * 16; 
 // Dynamic shared memory of the FP32 predictor: a fixed part (chunk results, per-warp staging,
 // sub-tet records) and, per cell, q and RHS rows followed by a ring of M_i^-1 stages that
 // takes whatever is left.  Returns the bytes needed for the largest cell with one stage.
+// Byte sizes of the fixed parts; the kernel carves its shared memory with the same functions.
+__host__ __device__ constexpr size_t f32_up128(size_t x) { return (x + 127) / 128 * 128; }
+__host__ __device__ constexpr size_t f32_sR_bytes(int N) {
+  return f32_up128((size_t)f32_chunk(N) * (N + 1) * np_of(N) * 5 * 4);
+}
+__host__ __device__ constexpr size_t f32_sB_bytes(int N) {
+  return f32_up128((size_t)f32_chunk(N) * 3 * np_of(N) * 5 * f32_ntp(N) * 4);
+}
 inline size_t f32_fixed_smem(int N, int Smax) {
-  const int Np = (N + 1) * (N + 2) * (N + 3) / 6;
-  auto up = [](size_t x) { return (x + 127) / 128 * 128; };
-  return up((size_t)kF32Chunk * (N + 1) * Np * 5 * 4) + up((size_t)kF32Warps * 3 * Np * 5 * 4) +
-         up((size_t)Smax * ((40 + 2 * Np + 15) / 16 * 16));
+  return f32_sR_bytes(N) + f32_sB_bytes(N) + f32_up128((size_t)Smax * f32_rec_bytes(N));
 }
 inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
   auto up = [](size_t x) { return (x + 127) / 128 * 128; };
-  return f32_fixed_smem(N, Smax) + 2 * up((size_t)Nmax * f32_row_stride(N) * 4) +
-         (size_t)kF32Rows * minv_ld(Nmax) * 4;
+  return f32_fixed_smem(N, Smax) + up((size_t)Nmax * f32_row_stride(N) * 4) +
+         up((size_t)Nmax * f32_rhs_stride(N) * 4) + (size_t)kF32Rows * minv_ld(Nmax) * 4;
 }
 
 // flux pre-contraction at one (sub-tet, time, local node j): out[d][v] = sum_e G[d][e] F_e[v]
@@ -159,9 +173,12 @@ template <int N>
 __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __grid_constant__ Batch bt,
                                                                         const RefData* __restrict__ ref,
                                                                         int diag, int smem_bytes) {
-  constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), NC = NT * 5, SR = f32_row_stride(N);
+  constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), SR = f32_row_stride(N);
+  constexpr int NTP = f32_ntp(N), SRN = f32_rhs_stride(N), CH = f32_chunk(N);
+  using VecT = typename std::conditional<NTP == 4, float4, float2>::type;
   constexpr int NPP = (NP + 3) / 4 * 4;  // rows of sSt padded to 16 bytes
-  constexpr int RG = kF32Threads / NT;   // 4-row groups per pass of the M_i^-1 apply
+  constexpr int MG = NPP / 4, TPN = NTP / 2;  // 4-row groups of R, time-slice pairs
+  static_assert(CH * 3 * NP * 5 * NTP >= kF32Warps * 3 * NP * 5, "epilogue staging must fit in sB");
   constexpr int REC = f32_rec_bytes(N);  // bytes per sub-tet record
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) float sSt[3][NP][NPP];  // sSt[d][j][m] = S^_d[m][j] (zero padded)
@@ -181,13 +198,13 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   auto up = [](size_t x) { return (x + 127) / 128 * 128; };
   unsigned char* p = smem_raw;
   float* sR = (float*)p;    // [CH][NT][NP][5]
-  p += up((size_t)kF32Chunk * NT * NP * 5 * 4);
-  float* sBw = (float*)p;   // [warps][3][NP][5]
-  p += up((size_t)kF32Warps * 3 * NP * 5 * 4);
+  p += f32_sR_bytes(N);
+  float* sBc = (float*)p;   // [CH][3 NP][5][NTP]; the epilogue uses it as [warps][3][NP][5]
+  p += f32_sB_bytes(N);
   unsigned char* srec = p;  // [S][REC] sub-tet records of the current cell
-  p += up((size_t)bt.Smax * REC);
-  unsigned char* const cell_base = p;  // per cell: sq [Ni][SR], srhs [Ni][SR], M_i^-1 ring
-  float* sB = sBw + warp * 3 * NP * 5;
+  p += f32_up128((size_t)bt.Smax * REC);
+  unsigned char* const cell_base = p;  // per cell: sq [Ni][SR], srhs [Ni][SRN], M_i^-1 ring
+  float* sB = sBc + warp * 3 * NP * 5;
   (void)Nmax;
 
   for (int e = tid; e < 3 * NP * NPP; e += kF32Threads) {
@@ -240,7 +257,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const uint32_t* inc = m.inc + m.inc_ptr[n0];
     float* sq = reinterpret_cast<float*>(cell_base);
     float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
-    float* ring = reinterpret_cast<float*>(cell_base + 2 * up((size_t)Ni * SR * 4));
+    float* ring = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4));
     const int stage_floats = kF32Rows * LD;
     const int nstage = min(kF32MaxStages,
                            (int)(((size_t)smem_bytes - (size_t)(reinterpret_cast<unsigned char*>(ring) - smem_raw)) /
@@ -269,6 +286,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         for (int v = 0; v < 5; ++v) uh[r][v] = 0.f;
       }
     }
+    if (NTP != NT)  // the padded time slices of RHS stay zero (so do those of Y)
+      for (int e = tid; e < Ni * SRN; e += kF32Threads) srhs[e] = 0.f;
     if (tid == 0 && !mbar_wait_bounded(&sbar, phase & 1u)) {
       atomicOr(&m.flags[F_TIMEOUT], 1);
       sAbort = 1;
@@ -291,8 +310,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       inode[r] = i < Ni * NT ? i / NT : -1;
       cur[r] = cend[r] = 0;
     }
-    constexpr int RGC = kF32Consumers * 32 / NT;  // 4-row groups per pass of the consumers
-    const int tt = tid % NT, rg0 = tid / NT;
+    constexpr int RGC = kF32Consumers * 32 / 5;  // 4-row groups per pass of the consumers
+    const int vv = tid % 5, rg0 = tid / 5;
     const bool consumer = warp < kF32Consumers;
     const bool act0 = consumer && rg0 < RGC && 4 * rg0 < Ni;
     const bool act1 = consumer && rg0 < RGC && 4 * (rg0 + RGC) < Ni;
@@ -312,44 +331,45 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           cend[r] = (int)(m.inc_ptr[n0 + inode[r] + 1] - m.inc_ptr[n0]);
         }
       }
-      for (int kc = 0; kc < S; kc += kF32Chunk) {
-        const int nk = min(kF32Chunk, S - kc);
-        for (int pr = warp; pr < nk * NT; pr += kF32Warps) {
-          const int kl = pr / NT, t = pr % NT;
-          const float* g = rec_g(kc + kl);
-          const uint16_t* Ak = rec_a(kc + kl);
-          if (lane < NP) {
-            float out[3][5];
-            f32_flux_contract<N>(sq, Ak, g, lane, t, visc, mu, kap, gam, Rg, dt, sD, out);
+      for (int kc = 0; kc < S; kc += CH) {
+        const int nk = min(CH, S - kc);
+        // (a) fluxes: items (k, j, t), t fastest (conflict-free stores into B)
+        for (int e = tid; e < nk * NP * NT; e += kF32Threads) {
+          const int t = e % NT, j = (e / NT) % NP, kl = e / (NT * NP);
+          float out[3][5];
+          f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt, sD, out);
+          float* dst = sBc + ((size_t)(kl * 3 * NP + j) * 5) * NTP + t;
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
+          for (int d = 0; d < 3; ++d)
 #pragma unroll
-              for (int v = 0; v < 5; ++v) sB[(d * NP + lane) * 5 + v] = out[d][v];
+            for (int v = 0; v < 5; ++v) dst[(d * NP * 5 + v) * NTP] = out[d][v];
+        }
+        __syncthreads();
+        // (b) R[k][t][m][v] = w_t sum_{d,j} S^_d[m][j] B[k][d j][v][t]: tile (k, v, time pair,
+        // rows 4mg..4mg+3), mg fastest
+        for (int e = tid; e < nk * 5 * TPN * MG; e += kF32Threads) {
+          const int mg = e % MG, tp = (e / MG) % TPN, v = (e / (MG * TPN)) % 5, kl = e / (MG * TPN * 5);
+          float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+          const float* bcol = sBc + ((size_t)kl * 3 * NP * 5 + v) * NTP + 2 * tp;
+          const float* scol = &sSt[0][0][4 * mg];
+#pragma unroll 6
+          for (int kk = 0; kk < 3 * NP; ++kk) {
+            const float4 s4 = *reinterpret_cast<const float4*>(scol + kk * NPP);
+            const float2 b2 = *reinterpret_cast<const float2*>(bcol + kk * 5 * NTP);
+            a0[0] += s4.x * b2.x; a0[1] += s4.y * b2.x; a0[2] += s4.z * b2.x; a0[3] += s4.w * b2.x;
+            a1[0] += s4.x * b2.y; a1[1] += s4.y * b2.y; a1[2] += s4.z * b2.y; a1[3] += s4.w * b2.y;
           }
-          __syncwarp();
-          // R[m][v] = w_t sum_d sum_j S^_d[m][j] B[d][j][v]: lane (mg, v) forms rows 4mg..4mg+3
-          if (lane < (NPP / 4) * 5) {
-            const int mg = lane / 5, v = lane % 5;
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll 5
-              for (int j = 0; j < NP; ++j) {
-                const float4 s4 = *reinterpret_cast<const float4*>(&sSt[d][j][4 * mg]);
-                const float b = sB[(d * NP + j) * 5 + v];
-                acc.x += s4.x * b;
-                acc.y += s4.y * b;
-                acc.z += s4.z * b;
-                acc.w += s4.w * b;
-              }
-            float* dst = sR + ((kl * NT + t) * NP + 4 * mg) * 5 + v;
+          for (int h = 0; h < 2; ++h) {
+            const int t = 2 * tp + h;
+            if (t >= NT) continue;
             const float wt = sW[t];
-            const float av[4] = {acc.x, acc.y, acc.z, acc.w};
+            float* dst = sR + ((kl * NT + t) * NP + 4 * mg) * 5 + v;
+            const float* av = h == 0 ? a0 : a1;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
               if (4 * mg + i < NP) dst[5 * i] = wt * av[i];
           }
-          __syncwarp();
         }
         __syncthreads();
         // gather this chunk's incidences, in (k, j) order, into the items' registers
@@ -374,21 +394,22 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         if (inode[r] < 0) continue;
         const int t = (tid + r * kF32Threads) % NT;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) srhs[inode[r] * SR + t * 5 + v] = racc[r][v];
+        for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v * NTP + t] = racc[r][v];
       }
       __syncthreads();
       // ---- 2. Y = M_i^-1 RHS.  The last warp streams M_i^-1 through a ring of shared-memory
       // stages (cp.async.bulk, full/empty mbarriers); the other warps never wait for each
-      // other inside the apply.  Consumer thread (row group rg, time slice t) keeps the 4 x 5
-      // tiles Y[4rg..4rg+3][t][0..4] of two row groups (M_i^-1 is symmetric: row l of a stage
-      // serves column l).
-      float acc[2][4][5];
+      // other inside the apply.  Consumer thread (row group rg, variable v) keeps the 4 x NTP
+      // tiles Y[4rg..4rg+3][v][0..NTP) of two row groups; per stage row it reads one float4
+      // of M_i^-1 and one vector of RHS (M_i^-1 is symmetric: row l of a stage serves
+      // column l).
+      float acc[2][4][NTP];
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int v = 0; v < 5; ++v) acc[r][i][v] = 0.f;
+          for (int t = 0; t < NTP; ++t) acc[r][i][t] = 0.f;
       if (!consumer) {
         if (lane == 0) {
           for (int b = 0; b < nblk && !sAbort; ++b) {
@@ -441,32 +462,27 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           for (int r = 0; r < 2; ++r) {
             if (!(r == 0 ? act0 : act1)) continue;
             const float* scol = stage + 4 * (rg0 + r * RGC);
-            const float* xrow = srhs + l0 * SR + tt * 5;
+            const float* xrow = srhs + l0 * SRN + vv * NTP;
+            auto fma_row = [&](int lr) {
+              const float4 a = *reinterpret_cast<const float4*>(scol + lr * LD);
+              const VecT xv = *reinterpret_cast<const VecT*>(xrow + lr * SRN);
+              const float av[4] = {a.x, a.y, a.z, a.w};
+              float xs[NTP];
+              if constexpr (NTP == 4) {
+                xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
+              } else {
+                xs[0] = xv.x; xs[1] = xv.y;
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int t = 0; t < NTP; ++t) acc[r][i][t] += av[i] * xs[t];
+            };
             if (rb == kF32Rows) {
 #pragma unroll
-              for (int lr = 0; lr < kF32Rows; ++lr) {
-                const float4 a = *reinterpret_cast<const float4*>(scol + lr * LD);
-                const float* x = xrow + lr * SR;
-                const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                  const float xv = x[v];
-#pragma unroll
-                  for (int i = 0; i < 4; ++i) acc[r][i][v] += av[i] * xv;
-                }
-              }
+              for (int lr = 0; lr < kF32Rows; ++lr) fma_row(lr);
             } else {
-              for (int lr = 0; lr < rb; ++lr) {
-                const float4 a = *reinterpret_cast<const float4*>(scol + lr * LD);
-                const float* x = xrow + lr * SR;
-                const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                  const float xv = x[v];
-#pragma unroll
-                  for (int i = 0; i < 4; ++i) acc[r][i][v] += av[i] * xv;
-                }
-              }
+              for (int lr = 0; lr < rb; ++lr) fma_row(lr);
             }
           }
           __syncwarp();
@@ -489,9 +505,15 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int n = 4 * g + i;
-          if (n < Ni)
-#pragma unroll
-            for (int v = 0; v < 5; ++v) srhs[n * SR + tt * 5 + v] = acc[r][i][v];
+          if (n < Ni) {
+            VecT y;
+            if constexpr (NTP == 4) {
+              y.x = acc[r][i][0]; y.y = acc[r][i][1]; y.z = acc[r][i][2]; y.w = acc[r][i][3];
+            } else {
+              y.x = acc[r][i][0]; y.y = acc[r][i][1];
+            }
+            *reinterpret_cast<VecT*>(srhs + n * SRN + vv * NTP) = y;
+          }
         }
       }
       __syncthreads();
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
 #pragma unroll
         for (int t = 0; t < NT; ++t)
 #pragma unroll
-          for (int v = 0; v < 5; ++v) y[t][v] = srhs[n * SR + t * 5 + v];
+          for (int v = 0; v < 5; ++v) y[t][v] = srhs[n * SRN + v * NTP + t];
 #pragma unroll
         for (int s2 = 0; s2 < NT; ++s2)
 #pragma unroll
@@ -557,7 +579,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         vend[r] = (int)(m.inc_ptr[n0 + n + 1] - m.inc_ptr[n0]);
       }
     }
-    const int CHV = kF32Chunk * NT;  // sub-tets per volume chunk (sR holds CH*NT slices)
+    const int CHV = CH * NT;  // sub-tets per volume chunk (sR holds CH*NT slices)
     for (int kc = 0; kc < S; kc += CHV) {
       const int nk = min(CHV, S - kc);
       for (int kl = warp; kl < nk; kl += kF32Warps) {
