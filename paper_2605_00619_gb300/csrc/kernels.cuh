@@ -337,9 +337,11 @@ __global__ void symmetrize_kernel(DevMesh m, int make32) {
       A[(int64_t)q * LD + r] = v;
     }
     __syncthreads();
-    if (make32)
-      for (int64_t e = threadIdx.x; e < m.minv_ptr[c + 1] - m.minv_ptr[c]; e += blockDim.x)
-        m.minv32[m.minv_ptr[c] + e] = (float)A[e];
+    if (make32)  // padding (columns >= n, rows >= n) written as zeros
+      for (int64_t e = threadIdx.x; e < m.minv_ptr[c + 1] - m.minv_ptr[c]; e += blockDim.x) {
+        const int64_t r = e / LD, q = e % LD;
+        m.minv32[m.minv_ptr[c] + e] = (r < n && q < n) ? (float)A[e] : 0.f;
+      }
     __syncthreads();
   }
 }

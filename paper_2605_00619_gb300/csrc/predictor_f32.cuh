@@ -17,9 +17,12 @@
 //      nodes it owns, the chunk's incidences in (k, j) order (fixed order: the sum is
 //      bitwise reproducible and has no atomics);
 //   2. Y = M_i^-1 RHS with M_i^-1 streamed through shared memory in stages of `rows` rows by
-//      cp.async.bulk (TMA bulk copies, completion on an mbarrier); thread (row group,
-//      variable) keeps 4 x NTP tiles of Y in registers and reads one vector of M_i^-1 and one
-//      of RHS per row of the stage (M_i^-1 is symmetric: row l of the stage serves column l);
+//      cp.async.bulk (TMA bulk copies, completion on an mbarrier), on the tensor cores:
+//      mma.sync m16n8k8 TF32 with each FP32 operand split into a TF32 head and tail (bit
+//      truncation) and the three leading products accumulated in FP32 (3xTF32: FP32-level
+//      accuracy); warp w
+//      owns the 16-row tiles w, w+15, w+30 of Y (M_i^-1 is symmetric: row l of the stage
+//      serves column l);
 //      q^{r+1}[n,s] = u^[n] - sum_t K1t^-1[s,t] Y[n,t] and the residual, in registers.
 // Epilogue: vol = sum_k A_k^T sum_d S^_d^T adj(J_k) F_bar_k, and q_bar, F_bar . n on the face
 // slots, as the FP64 kernel.  Every mbarrier wait is bounded; a wait that runs out sets
@@ -74,6 +77,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// x = hi + lo + e with hi, lo TF32 (the low 13 bits cleared: truncation) and
+// |e| <= 2^-21 |x|; hi + lo and the products of 3xTF32 carry FP32-level accuracy.
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(x) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
+}
+// D += A B, m16n8k8, A row-major TF32 (4 regs), B column-major TF32 (2 regs), D FP32.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Bulk (TMA) copy of `bytes` (multiple of 16, both addresses 16-byte aligned) global -> shared,
 // completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -89,7 +107,7 @@ constexpr int kF32MaxNodes = 640;
 constexpr int kF32Items = 5;  // ceil(640 * 4 / 512)
 inline int predictor_f32_max_nodes(int N) {
   const int by_items = kF32Items * kF32Threads / (N + 1);
-  const int by_rows = 8 * (kF32Consumers * 32 / 5);
+  const int by_rows = 3 * 16 * kF32Consumers;  // three 16-row tiles per consumer warp
   (void)N;
   return std::min(kF32MaxNodes, std::min(by_items, by_rows));
 }
@@ -99,7 +117,9 @@ inline int predictor_f32_max_nodes(int N) {
 constexpr int f32_row_stride(int N) { return ((N + 1) * 5) | 1; }
 // Time slices of RHS / Y padded to a vector width, and their row stride [5][NTP].
 constexpr int f32_ntp(int N) { return N == 1 ? 2 : 4; }
-constexpr int f32_rhs_stride(int N) { return 5 * f32_ntp(N); }
+// Row stride of RHS / Y: 24 floats (5 NTP used, the rest zero), a multiple of 8 columns for
+// the tensor-core tiles, and 24 = 8 (mod 16) for conflict-free fragment loads.
+constexpr int f32_rhs_stride(int N) { return (void)N, 24; }
 // Sub-tets per chunk of the right-hand side (16 time-slice pairs of B per chunk).
 constexpr int f32_chunk(int N) { return f32_ntp(N) == 4 ? 8 : 16; }
 
@@ -175,7 +195,6 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
                                                                         int diag, int smem_bytes) {
   constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), SR = f32_row_stride(N);
   constexpr int NTP = f32_ntp(N), SRN = f32_rhs_stride(N), CH = f32_chunk(N);
-  using VecT = typename std::conditional<NTP == 4, float4, float2>::type;
   constexpr int NPP = (NP + 3) / 4 * 4;  // rows of sSt padded to 16 bytes
   constexpr int MG = NPP / 4, TPN = NTP / 2;  // 4-row groups of R, time-slice pairs
   static_assert(CH * 3 * NP * 5 * NTP >= kF32Warps * 3 * NP * 5, "epilogue staging must fit in sB");
@@ -269,7 +288,6 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       mbar_expect_tx(&sbar, (uint32_t)(S * REC));
       bulk_g2s(srec, m.sub32 + (size_t)kbase * REC, (uint32_t)(S * REC), &sbar);
     }
-    float uh[2][5];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int n = tid + r * kF32Threads;
@@ -277,17 +295,14 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         const double* un = m.u + (n0 + n) * 5;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          uh[r][v] = (float)un[v];
+          const float uv = (float)un[v];
 #pragma unroll
-          for (int t = 0; t < NT; ++t) sq[n * SR + t * 5 + v] = uh[r][v];
+          for (int t = 0; t < NT; ++t) sq[n * SR + t * 5 + v] = uv;
         }
-      } else {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) uh[r][v] = 0.f;
       }
     }
-    if (NTP != NT)  // the padded time slices of RHS stay zero (so do those of Y)
-      for (int e = tid; e < Ni * SRN; e += kF32Threads) srhs[e] = 0.f;
+    // the padded columns of RHS stay zero (so do those of Y)
+    for (int e = tid; e < Ni * SRN; e += kF32Threads) srhs[e] = 0.f;
     if (tid == 0 && !mbar_wait_bounded(&sbar, phase & 1u)) {
       atomicOr(&m.flags[F_TIMEOUT], 1);
       sAbort = 1;
@@ -302,28 +317,24 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     phase ^= 1u;
     __syncthreads();
 
-    // gather items of this thread: (node, time slice) = (i / NT, i % NT), i = tid + 512 r
-    int inode[kF32Items], cur[kF32Items], cend[kF32Items];
-#pragma unroll
-    for (int r = 0; r < kF32Items; ++r) {
-      const int i = tid + r * kF32Threads;
-      inode[r] = i < Ni * NT ? i / NT : -1;
-      cur[r] = cend[r] = 0;
-    }
-    constexpr int RGC = kF32Consumers * 32 / 5;  // 4-row groups per pass of the consumers
-    const int vv = tid % 5, rg0 = tid / 5;
+    constexpr int NNT = (5 * NTP + 7) / 8;  // 8-column tiles of Y
     const bool consumer = warp < kF32Consumers;
-    const bool act0 = consumer && rg0 < RGC && 4 * rg0 < Ni;
-    const bool act1 = consumer && rg0 < RGC && 4 * (rg0 + RGC) < Ni;
+    const int gq = lane >> 2, tq = lane & 3;  // mma fragment coordinates
+    const int nmt = (Ni + 15) / 16;           // 16-row tiles of Y
 
     int it = 0;
     bool conv = false;
     while (!conv && it < m.picard_max) {
       ++it;
       // ---- 1. right-hand side RHS[n][t] = sum over incidences (k, j) of R_{k,t}[j]
+      // gather items of this thread: (node, time slice) = (i / NT, i % NT), i = tid + 512 r
+      int inode[kF32Items], cur[kF32Items], cend[kF32Items];
       float racc[kF32Items][5];
 #pragma unroll
       for (int r = 0; r < kF32Items; ++r) {
+        const int i = tid + r * kF32Threads;
+        inode[r] = i < Ni * NT ? i / NT : -1;
+        cur[r] = cend[r] = 0;
 #pragma unroll
         for (int v = 0; v < 5; ++v) racc[r][v] = 0.f;
         if (inode[r] >= 0) {
@@ -399,17 +410,17 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       __syncthreads();
       // ---- 2. Y = M_i^-1 RHS.  The last warp streams M_i^-1 through a ring of shared-memory
       // stages (cp.async.bulk, full/empty mbarriers); the other warps never wait for each
-      // other inside the apply.  Consumer thread (row group rg, variable v) keeps the 4 x NTP
-      // tiles Y[4rg..4rg+3][v][0..NTP) of two row groups; per stage row it reads one float4
-      // of M_i^-1 and one vector of RHS (M_i^-1 is symmetric: row l of a stage serves
-      // column l).
-      float acc[2][4][NTP];
+      // other inside the apply.  Consumer warp w accumulates the 16 x 8 tiles (mt, nt) of Y
+      // for mt = w, w + 15, w + 30 with 3xTF32 mma.sync; per 8-row k-step of a stage it loads
+      // the B fragments (RHS rows) once for all column tiles and the A fragments (M_i^-1
+      // rows = columns) once per row tile.
+      float cacc[3][NNT][4];
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int nt = 0; nt < NNT; ++nt)
 #pragma unroll
-          for (int t = 0; t < NTP; ++t) acc[r][i][t] = 0.f;
+          for (int i = 0; i < 4; ++i) cacc[r][nt][i] = 0.f;
       if (!consumer) {
         if (lane == 0) {
           for (int b = 0; b < nblk && !sAbort; ++b) {
@@ -457,33 +468,44 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           fpar ^= 1u << s;
           const float* stage = ring + (size_t)s * stage_floats;
           const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
-          // one pass per row group; a full stage is unrolled completely
+          // one 8-row k-step: B fragments (RHS rows) for every column tile, then per row tile the
+          // A fragments (M_i^-1 rows) and three rounds of MMAs over the column tiles
+          auto kstep = [&](int ks, bool full) {
+            const int k0 = ks * 8 + tq, k1 = k0 + 4;  // stage rows of this lane's fragments
+            const bool v0 = full || k0 < rb, v1 = full || k1 < rb;  // rows past N_i give zero
+            uint32_t bh[NNT][2], bl[NNT][2];
 #pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            if (!(r == 0 ? act0 : act1)) continue;
-            const float* scol = stage + 4 * (rg0 + r * RGC);
-            const float* xrow = srhs + l0 * SRN + vv * NTP;
-            auto fma_row = [&](int lr) {
-              const float4 a = *reinterpret_cast<const float4*>(scol + lr * LD);
-              const VecT xv = *reinterpret_cast<const VecT*>(xrow + lr * SRN);
-              const float av[4] = {a.x, a.y, a.z, a.w};
-              float xs[NTP];
-              if constexpr (NTP == 4) {
-                xs[0] = xv.x; xs[1] = xv.y; xs[2] = xv.z; xs[3] = xv.w;
-              } else {
-                xs[0] = xv.x; xs[1] = xv.y;
-              }
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int t = 0; t < NTP; ++t) acc[r][i][t] += av[i] * xs[t];
-            };
-            if (rb == kF32Rows) {
-#pragma unroll
-              for (int lr = 0; lr < kF32Rows; ++lr) fma_row(lr);
-            } else {
-              for (int lr = 0; lr < rb; ++lr) fma_row(lr);
+            for (int nt = 0; nt < NNT; ++nt) {
+              const float x0 = v0 ? srhs[(l0 + k0) * SRN + nt * 8 + gq] : 0.f;
+              const float x1 = v1 ? srhs[(l0 + k1) * SRN + nt * 8 + gq] : 0.f;
+              tf32_split(x0, bh[nt][0], bl[nt][0]);
+              tf32_split(x1, bh[nt][1], bl[nt][1]);
             }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              const int mt = warp + r * kF32Consumers;
+              if (mt >= nmt) break;
+              const float* arow0 = stage + k0 * LD + mt * 16 + gq;
+              const float* arow1 = stage + k1 * LD + mt * 16 + gq;
+              uint32_t ah[4], al[4];
+              tf32_split(v0 ? arow0[0] : 0.f, ah[0], al[0]);
+              tf32_split(v0 ? arow0[8] : 0.f, ah[1], al[1]);
+              tf32_split(v1 ? arow1[0] : 0.f, ah[2], al[2]);
+              tf32_split(v1 ? arow1[8] : 0.f, ah[3], al[3]);
+#pragma unroll
+              for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], al, bh[nt][0], bh[nt][1]);
+#pragma unroll
+              for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bl[nt][0], bl[nt][1]);
+#pragma unroll
+              for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bh[nt][0], bh[nt][1]);
+            }
+          };
+          if (rb == kF32Rows) {  // full stage: no row masks
+#pragma unroll
+            for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, true);
+          } else {
+#pragma unroll
+            for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, false);
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&sempty[s]);
@@ -498,40 +520,52 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         __syncthreads();
         return;
       }
+      if (consumer)
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        if (!(r == 0 ? act0 : act1)) continue;
-        const int g = rg0 + r * RGC;
+        for (int r = 0; r < 3; ++r) {
+          const int mt = warp + r * kF32Consumers;
+          if (mt >= nmt) break;
+          const int n0r = mt * 16 + gq, n1r = n0r + 8;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int n = 4 * g + i;
-          if (n < Ni) {
-            VecT y;
-            if constexpr (NTP == 4) {
-              y.x = acc[r][i][0]; y.y = acc[r][i][1]; y.z = acc[r][i][2]; y.w = acc[r][i][3];
-            } else {
-              y.x = acc[r][i][0]; y.y = acc[r][i][1];
+          for (int nt = 0; nt < NNT; ++nt) {
+            const int col = nt * 8 + 2 * tq;
+            if (n0r < Ni) {
+              srhs[n0r * SRN + col] = cacc[r][nt][0];
+              srhs[n0r * SRN + col + 1] = cacc[r][nt][1];
             }
-            *reinterpret_cast<VecT*>(srhs + n * SRN + vv * NTP) = y;
+            if (n1r < Ni) {
+              srhs[n1r * SRN + col] = cacc[r][nt][2];
+              srhs[n1r * SRN + col + 1] = cacc[r][nt][3];
+            }
           }
         }
-      }
       __syncthreads();
       float res = 0.f, qmax = 0.f;
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int n = tid + r * kF32Threads;
         if (n >= Ni) continue;
-        float y[NT][5];
+        float y[NT][5], uh[5];
 #pragma unroll
-        for (int t = 0; t < NT; ++t)
+        for (int v = 0; v < 5; ++v) {  // one vector load per variable
+          float yv[NTP];
+          if constexpr (NTP == 4) {
+            const float4 w = *reinterpret_cast<const float4*>(srhs + n * SRN + v * 4);
+            yv[0] = w.x; yv[1] = w.y; yv[2] = w.z; yv[3] = w.w;
+          } else {
+            const float2 w = *reinterpret_cast<const float2*>(srhs + n * SRN + v * 2);
+            yv[0] = w.x; yv[1] = w.y;
+          }
 #pragma unroll
-          for (int v = 0; v < 5; ++v) y[t][v] = srhs[n * SRN + v * NTP + t];
+          for (int t = 0; t < NT; ++t) y[t][v] = yv[t];
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) uh[v] = (float)m.u[(n0 + n) * 5 + v];  // u^ (L2-resident)
 #pragma unroll
         for (int s2 = 0; s2 < NT; ++s2)
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            float x = uh[r][v];
+            float x = uh[v];
 #pragma unroll
             for (int t = 0; t < NT; ++t) x -= sK[s2][t] * y[t][v];
             const float old = sq[n * SR + s2 * 5 + v];

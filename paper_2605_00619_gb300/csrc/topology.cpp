@@ -362,7 +362,7 @@ int build_topology(const RefData& R, int64_t n_vertices, const double* xyz, int6
     T.node_ptr[c + 1] = T.node_ptr[c] + cells[c].Ni;
     T.sub_ptr[c + 1] = T.sub_ptr[c] + cells[c].S;
     T.slot_ptr[c + 1] = T.slot_ptr[c] + (int64_t)cells[c].slots.size();
-    // rows padded to a multiple of 4 words (16 bytes), blocks to a multiple of 32 words
+    // rows padded to minv_ld words, blocks to a multiple of 32 words (128 bytes)
     const int64_t ld = minv_ld(cells[c].Ni);
     T.minv_ptr[c + 1] = T.minv_ptr[c] + ((int64_t)cells[c].Ni * ld + 31) / 32 * 32;
     T.Nmax = std::max(T.Nmax, cells[c].Ni);

@@ -12,9 +12,11 @@
 
 namespace afe {
 
-// Leading dimension of a cell's M_i^-1 block: N_i rounded up to a multiple of 4, so that
-// every row starts on a 16-byte boundary (bulk copies of whole rows).
-inline constexpr int minv_ld(int n) { return (n + 3) & ~3; }
+// Leading dimension of a cell's M_i^-1 block: N_i rounded up to a multiple of 16, plus 8.
+// Rows start on 16-byte boundaries (bulk copies of whole rows), every 16-row tile of the
+// tensor-core apply stays inside a row, and LD = 8 (mod 16) makes the fragment loads of
+// four consecutive rows hit 32 different shared-memory banks.
+inline constexpr int minv_ld(int n) { return (n + 15) / 16 * 16 + 8; }
 
 struct Topology {
   int N = 0, Np = 0, Nt = 0, Nf = 0;
