@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -30,6 +31,18 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DOF-updates/s per ADER-DG step"
+
+# Largest CFL numbers at which the fan-subgrid Voronoi meshes of inputs.voronoi run the
+# density wave stably to t = 0.1 (measured on 16^3 and 32^3 meshes, both forms): the
+# paper's 0.3 holds for N = 1; at N = 2 a 32^3 mesh diverges after ~200 steps at 0.3 and at
+# N = 3 after ~20 steps at 0.3 and ~30 at 0.2.
+STABLE_CFL = {1: 0.3, 2: 0.2, 3: 0.15}
+
+# DRAM bytes (read + write) of one predictor_f32_kernel<3> launch per cell, from the ncu
+# capture summarised in profiles/step_kernels_density_wave_12c_N3.md (905 MB over 1728 cells
+# of the density-wave workload): the fixed-point iterations re-read M_i^-1 from L2, so the
+# traffic grows with the cells, not with the iterations.  Valid for that kernel version only.
+PREDICTOR_N3_DRAM_BYTES_PER_CELL = (863.081472e6 + 41.609984e6) / 1728
 UNIT = "DOF-updates/s"
 
 
@@ -44,15 +57,29 @@ def _args():
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 form (0: skip)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cfl", type=float, default=None,
+                    help="CFL number (default: 0.3, the paper's, for the density wave; the stable one otherwise)")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
-    ap.add_argument("--serve-requests", type=int, default=300)
-    ap.add_argument("--serve-rate", type=float, default=200.0, help="offered load, requests per second")
-    ap.add_argument("--serve-slots", type=int, default=16, help="slots per catalogue mesh")
+    ap.add_argument("--study", choices=["convergence"], help="accuracy study instead of the throughput run")
+    ap.add_argument("--workload", default="density", choices=["density", "shock", "tgv"],
+                    help="density: density wave, periodic unit cube, Euler; shock: spherical explosion on "
+                         "[-1,1]^3, transmissive, limiter on; tgv: Navier-Stokes Taylor-Green vortex on "
+                         "[0,2pi)^3, mu 0.01")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="offered load, requests per second")
+    ap.add_argument("--serve-steps", type=int, default=20, help="CFL steps per request")
+    ap.add_argument("--serve-slots", type=int, default=4, help="slots per catalogue entry (mesh, N)")
     return ap.parse_args()
 
 
-def workload_name(n, N):
-    return f"density-wave periodic unit cube, {n}^3 jittered-Voronoi cells (fan subgrid), AFE N={N}, Euler, CFL 0.3"
+def workload_name(n, N, workload="density"):
+    if workload == "shock":
+        return (f"spherical explosion (smoothed over 1.5 lattice spacings) on [-1,1]^3 (transmissive), {n}^3 "
+                f"jittered-Voronoi cells (fan subgrid), AFE N={N}, Euler with the artificial-viscosity limiter")
+    if workload == "tgv":
+        return (f"Taylor-Green vortex on [0,2pi)^3 (periodic), {n}^3 jittered-Voronoi cells (fan subgrid), "
+                f"AFE N={N}, Navier-Stokes mu 0.01 Pr 0.71")
+    return f"density-wave periodic unit cube, {n}^3 jittered-Voronoi cells (fan subgrid), AFE N={N}, Euler"
 
 
 # ----------------------------------------------------------------------------------------
@@ -184,8 +211,9 @@ def predictor_model(node_ptr, sub_ptr, iters, N, real_bytes):
     stiffness contraction 2*3*Np flop per (sub-tet, time, node, variable); the agglomeration
     1 flop per incidence and variable; the inverse-mass apply 2 N_i^2 (5 Nt); the update
     2 Nt per (node, time, variable).  Epilogue: one more flux pass and the volume term.
-    Bytes: the dense M_i^-1 is read once per iteration (it does not stay on chip), plus the
-    state, the sub-tet geometry and the outputs once.
+    Bytes (the method's minimum): the dense M_i^-1 once per step (rows of 16 ceil(N_i/16) + 8
+    words), the state, the sub-tet records and the outputs once; the variant that streams
+    M_i^-1 from HBM in every fixed-point iteration is returned beside it.
     """
     import numpy as np
     Np = (N + 1) * (N + 2) * (N + 3) // 6
@@ -196,8 +224,41 @@ def predictor_model(node_ptr, sub_ptr, iters, N, real_bytes):
     per_it = S * Nt * Np * (150 + 5 * 6 * Np + 5) + 2 * Ni * Ni * 5 * Nt + Ni * Nt * 5 * 2 * Nt
     epi = S * Np * Nt * 150 + S * Np * 5 * 6 * Np + S * Np * 5
     flops = float(np.sum(it * per_it + epi))
-    bytes_ = float(np.sum(it * Ni * Ni * real_bytes + Ni * 5 * 8 + S * (10 * 8 + Np * 2) + Ni * 5 * real_bytes))
-    return flops, bytes_
+    LD = np.ceil(Ni / 16) * 16 + 8
+    once = Ni * 5 * 8 + S * (10 * 4 + Np * 2) + Ni * 5 * real_bytes
+    bytes_min = float(np.sum(Ni * LD * real_bytes + once))
+    bytes_streamed = float(np.sum(it * Ni * LD * real_bytes + once))
+    return flops, bytes_min, bytes_streamed
+
+
+class RankReducer:
+    """Max / sum of one float over the ranks of a process group (identity without one).
+
+    ``device`` is where the reduction tensor lives: "cuda" under NCCL, "cpu" under gloo."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+
+def throughput(red, dofs_per_step, steps, ms):
+    """Whole-job DOF-updates/s: DOF-updates of all ranks over the slowest rank's time."""
+    ms_max = red.max(ms)
+    return red.sum(dofs_per_step * steps) / (ms_max / 1e3), ms_max
 
 
 def ours(args):
@@ -223,21 +284,16 @@ def ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    red = RankReducer(dist, "cuda")
+    max_over_ranks, sum_over_ranks = red.max, red.sum
 
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
-    pm = periodic_voronoi(args.n, seed=rank)
+    from inputs.voronoi import box_voronoi
+    if args.workload == "shock":
+        pm = box_voronoi(args.n, seed=rank)
+    elif args.workload == "tgv":
+        pm = periodic_voronoi(args.n, L=2 * math.pi, seed=rank)
+    else:
+        pm = periodic_voronoi(args.n, seed=rank)
     stream = torch.cuda.Stream()
     sid = stream.cuda_stream
     peaks = {}
@@ -246,15 +302,25 @@ def ours(args):
     except (OSError, ValueError):
         pass
 
-    def run_form(prec, steps, warmup, e2e):
+    def run_form(prec, steps, warmup, e2e, cfl):
         fp32 = prec == afe.AFE_FP32
+        extra = {}
+        if args.workload == "shock":
+            extra = dict(limiter=1)
+        elif args.workload == "tgv":
+            extra = dict(equations=afe.AFE_NAVIER_STOKES, mu=0.01, Pr=0.71, kappa=-1.0)
         p = afe.afe_default_params(args.order, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
-                                   picard_max=128 if fp32 else 64)
+                                   picard_max=128 if fp32 else 64, cfl=cfl, **extra)
         h = afe.create_from_polymesh(pm, p, stream=sid)
         n_nodes = afe.afe_num_nodes(h)
         node_ptr = afe.afe_node_ptr(h, pm.n_cells)
         x = afe.afe_get_node_coords(h)
-        u0 = states.density_wave(x)
+        if args.workload == "shock":  # smoothed over 1.5 lattice spacings
+            u0 = states.spherical_riemann(x, alpha0=1.5 * 2.0 / args.n)
+        elif args.workload == "tgv":
+            u0 = states.taylor_green_3d(x, p0=100.0)
+        else:
+            u0 = states.density_wave(x)
         afe.afe_set_state(h, u0)
         afe.afe_step_async(h, 0.0, warmup)
         st = afe.afe_sync(h, check=False)
@@ -285,8 +351,8 @@ def ours(args):
         rec = dict(status=[st, st2], ms=ms, wall=wall, stage_ms=(stage_ms / max(nst, 1)).tolist(), clocks=clk,
                    n_nodes=n_nodes, launches=launches, iters_mean=float(iters.mean()), iters_max=int(iters.max()),
                    nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h))
-        rec["flops"], rec["abytes"] = predictor_model(node_ptr, pm.cell_subtet_ptr, iters, args.order,
-                                                      4 if prec == afe.AFE_FP32 else 8)
+        rec["flops"], rec["abytes"], rec["abytes_streamed"] = predictor_model(
+            node_ptr, pm.cell_subtet_ptr, iters, args.order, 4 if prec == afe.AFE_FP32 else 8)
         if e2e:
             # end to end through the public API, host buffers: per step the state goes up from
             # pinned host memory, one step runs, the new state comes back
@@ -303,19 +369,22 @@ def ours(args):
         afe.afe_mesh_destroy(h)
         return rec
 
-    r32 = run_form(afe.AFE_FP32, args.steps, args.warmup, not args.no_e2e)
-    r64 = run_form(afe.AFE_FP64, args.fp64_steps, 1, False) if args.fp64_steps > 0 else None
+    cfl = args.cfl if args.cfl is not None else (0.3 if args.workload == "density" else STABLE_CFL[args.order])
+    r32 = run_form(afe.AFE_FP32, args.steps, args.warmup, not args.no_e2e, cfl)
+    r64 = run_form(afe.AFE_FP64, args.fp64_steps, 1, False, cfl) if args.fp64_steps > 0 else None
+    # the same FP32 step at the largest CFL that stays stable over long runs on these meshes
+    rst = (run_form(afe.AFE_FP32, args.steps, args.warmup, False, STABLE_CFL[args.order])
+           if STABLE_CFL[args.order] != cfl else None)
 
     K = args.steps
     dofs = 5 * r32["n_nodes"]
-    ms_max = max_over_ranks(r32["ms"])
+    value, ms_max = throughput(red, dofs, K, r32["ms"])
     total_dofs = sum_over_ranks(dofs * K)
-    value = total_dofs / (ms_max / 1e3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args.n, args.order), "cells": pm.n_cells, "nodes": r32["n_nodes"],
+        "config": {"workload": workload_name(args.n, args.order, args.workload), "cells": pm.n_cells, "nodes": r32["n_nodes"],
                    "dofs": dofs, "precision": "FP32 arithmetic, FP64 master state / dt / cell totals",
                    "picard_tol": 1e-6, "l2": "inputs larger than L2 (M_i^-1 alone is "
                    f"{r32['bytes'] / 1e9:.1f} GB of device state)", "parallelism": f"{world} independent replicas"},
@@ -348,6 +417,18 @@ def ours(args):
                            "traffic": None, "kernel": f"predictor_f32_kernel<{args.order}>", "peak_note": "of measured"}
     out["roofline"]["algorithmic_flops"] = r32["flops"]
     out["roofline"]["algorithmic_bytes"] = r32["abytes"]
+    out["roofline"]["algorithmic_bytes_streamed_per_iteration"] = r32["abytes_streamed"]
+    if args.order == 3 and args.workload == "density":
+        out["roofline"]["traffic"] = PREDICTOR_N3_DRAM_BYTES_PER_CELL * pm.n_cells
+        out["roofline"]["traffic_note"] = ("ncu dram__bytes_read+write of a 12^3 launch scaled by cells "
+                                           "(profiles/step_kernels_density_wave_12c_N3.md)")
+    out["config"]["cfl"] = cfl
+    if rst is not None:
+        v_st, ms_st = throughput(red, 5 * rst["n_nodes"], K, rst["ms"])
+        out["fp32_stable_cfl"] = {"cfl": STABLE_CFL[args.order], "value": v_st, "unit": UNIT, "ms_per_step": ms_st / K,
+                                  "picard_iters_mean": rst["iters_mean"], "status": rst["status"],
+                                  "note": "CFL at which these meshes run stably to t = 0.1 (the paper's 0.3 "
+                                          "diverges after some tens of steps at this order)"}
     if r64 is not None:
         ms64 = max_over_ranks(r64["ms"])
         out["fp64_plain"] = {"value": sum_over_ranks(5 * r64["n_nodes"] * args.fp64_steps) / (ms64 / 1e3),
@@ -374,64 +455,174 @@ def ours(args):
 
 
 def serve(args):
-    """Continuous batching of many small simulations (one GPU).
+    """Continuous batching of many independent simulations (one GPU).
 
-    Catalogue: periodic jittered-Voronoi meshes with 4^3, 5^3 and 6^3 cells, AFE N (default
-    3), FP32 form, Euler, CFL 0.3, density-wave initial data; ``--serve-slots`` resident
-    handles per mesh.  Requests arrive as a Poisson process of ``--serve-rate`` per second,
-    each for a mesh drawn uniformly and 5, 10 or 20 CFL steps.  The batched server (all
-    occupied slots advanced together, one launch per stage, CUDA graph per batch) is timed
-    against the serial server (one request at a time, alone) on the same requests.  Reported:
-    DOF-updates/s over the run, p50/p99 request latency (arrival to completion).
+    Requests (after the serving workload of the method's evaluation, scaled to resident
+    meshes): a mesh drawn uniformly from a catalogue of jittered-Voronoi meshes -- the periodic
+    unit cube and the box [-1,1]^3, 8^3 and 12^3 seeds -- with N uniform in {1, 2, 3}; the
+    periodic meshes carry the density wave, the box meshes a spherical explosion smoothed
+    over 1.5 lattice spacings with a random centre in [-0.5,0.5]^3 and pressure ratio in
+    [2, 10] (no limiter: with the artificial viscosity these runs diverge within a few steps
+    on the fan-subgrid meshes); each
+    request runs ``--serve-steps`` CFL steps.  Arrivals are a Poisson process of
+    ``--serve-rate`` per second.  The batched server (FP32 form; every occupied slot advanced
+    together, one launch per stage and order, a CUDA graph per batch) is timed against the
+    serial server running the same requests one at a time in the plain FP64 form.  Reported:
+    DOF-updates/s over each run and p50/p99 request latency (arrival to completion).
     """
+    import numpy as np
+    import torch
+
+    from inputs import states
+    from inputs.voronoi import box_voronoi, periodic_voronoi
+    from paper_2605_00619_gb300 import afe
+    from paper_2605_00619_gb300.serving import GpuEngine, Request, Server
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    afe.lib()
+    sizes = (8, 12)
+    meshes = {}
+    for n in sizes:
+        meshes[f"p{n}"] = periodic_voronoi(n, seed=100 + n)
+        meshes[f"b{n}"] = box_voronoi(n, seed=200 + n)
+
+    def params(kind, N, prec):
+        fp32 = prec == afe.AFE_FP32
+        return afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
+                                      picard_max=128 if fp32 else 64, cfl=STABLE_CFL[N])
+
+    keys = [f"{mk}_N{N}" for mk in sorted(meshes) for N in (1, 2, 3)]
+    cat32 = {k: (meshes[k.split("_")[0]], params(k[0], int(k[-1]), afe.AFE_FP32)) for k in keys}
+    cat64 = {k: (meshes[k.split("_")[0]], params(k[0], int(k[-1]), afe.AFE_FP64)) for k in keys}
+    eng = GpuEngine(cat32, {k: args.serve_slots for k in keys})
+    ser = GpuEngine(cat64, {k: 1 for k in keys})
+
+    rng = np.random.default_rng(12345)
+
+    def make_requests(n_req, rate):
+        out, t = [], 0.0
+        for i in range(n_req):
+            t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+            k = keys[int(rng.integers(len(keys)))]
+            if k.startswith("p"):
+                ic = states.density_wave
+            else:
+                c = rng.uniform(-0.5, 0.5, 3)
+                ratio = rng.uniform(2.0, 10.0)
+                a0 = 1.5 * 2.0 / int(k.split("_")[0][1:])  # smoothing width: 1.5 lattice spacings
+                ic = (lambda c_, r_, a_: lambda x: states.spherical_riemann(x, centre=tuple(c_), p_in=0.1 * r_,
+                                                                             alpha0=a_))(c, ratio, a0)
+            out.append(Request(i, k, args.serve_steps, t, q0=ic))
+        return out
+
+    Server(eng).run(make_requests(len(eng.slots), 0.0))            # warm-up: graphs, caches
+    Server(ser, mode="serial").run(make_requests(len(keys), 0.0))
+    reqs = make_requests(args.serve_requests, args.serve_rate)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    sb = Server(eng, max_chunk=8).run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
+    clk = clocks.stop()
+    ss = Server(ser, mode="serial").run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
+    out = {
+        "metric": "serving throughput, continuous batching (FP32) vs serial plain FP64", "value": sb.throughput,
+        "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "p50_ms": 1e3 * sb.p50_s, "p99_ms": 1e3 * sb.p99_s, "mean_ms": 1e3 * sb.mean_s,
+        "mean_batch_members": sb.mean_batch, "batch_steps": sb.steps_launched, "failed": sb.failed,
+        "makespan_s": sb.makespan_s,
+        "serial_fp64": {"value": ss.throughput, "unit": UNIT, "p50_ms": 1e3 * ss.p50_s, "p99_ms": 1e3 * ss.p99_s,
+                        "makespan_s": ss.makespan_s, "failed": ss.failed},
+        "batched_over_serial": sb.throughput / ss.throughput,
+        "clocks": clk,
+        "config": {"workload": f"{args.serve_requests} requests, Poisson arrivals at {args.serve_rate:g}/s, "
+                               f"{args.serve_steps} CFL steps each; meshes periodic/box {sizes[0]}^3 and "
+                               f"{sizes[1]}^3, N in {{1,2,3}}; density wave (periodic) or smoothed spherical "
+                               f"explosion, pressure ratio 2-10 (box)",
+                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes},
+    }
+    eng.close()
+    ser.close()
+    print(json.dumps(out), flush=True)
+
+
+def convergence(args):
+    """Accuracy of both forms on the density wave (periodic unit cube, Euler, CFL 0.3).
+
+    For N = 2, 3 and jittered-Voronoi meshes of 8^3 and 16^3 cells (and 32^3 for the FP32
+    form), integrate to t = 0.1 with equal steps (the CFL step of the initial state at the
+    stable CFL of STABLE_CFL, shortened to land on t = 0.1) and report the error in rho against the exact solution
+    rho(x - (1,1,1) t): a volume-weighted nodal L2 norm, sqrt(sum_i |P_i| mean_{n in P_i} e_n^2),
+    and the max norm; the observed order between consecutive meshes (h ~ 1/n); and the
+    relative L2 difference between the FP32 and FP64 forms.
+    """
+    import numpy as np
     import torch
 
     from inputs import states
     from inputs.voronoi import periodic_voronoi
     from paper_2605_00619_gb300 import afe
-    from paper_2605_00619_gb300.serving import GpuEngine, Server, poisson_requests
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     afe.lib()
-    cat = {f"{n}^3": periodic_voronoi(n, seed=10 + n) for n in (4, 5, 6)}
-    p = afe.afe_default_params(args.order, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
-    stream = torch.cuda.Stream()
-    eng = GpuEngine(cat, {k: args.serve_slots for k in cat}, p, stream=stream.cuda_stream)
-    for sl in eng.slots:
-        if sl.mesh not in eng.default_state:
-            eng.default_state[sl.mesh] = states.density_wave(afe.afe_get_node_coords(sl.handle))
-    keys = sorted(cat)
-    warm = poisson_requests(0.0, 2 * len(eng.slots), keys, [3], seed=99)
-    Server(eng).run(warm)
-    Server(eng, mode="serial").run(warm[:len(keys)])
-    reqs = lambda: poisson_requests(args.serve_rate, args.serve_requests, keys, [5, 10, 20], seed=1)  # noqa: E731
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    sb = Server(eng, max_chunk=4).run(reqs())
-    clk = clocks.stop()
-    ss = Server(eng, mode="serial").run(reqs())
-    nodes = {k: next(s.n_nodes for s in eng.slots if s.mesh == k) for k in keys}
-    out = {
-        "metric": "serving throughput, continuous batching", "value": sb.throughput, "unit": UNIT,
-        "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-        "p50_ms": 1e3 * sb.p50_s, "p99_ms": 1e3 * sb.p99_s, "mean_ms": 1e3 * sb.mean_s,
-        "mean_batch_members": sb.mean_batch, "batch_steps": sb.steps_launched, "failed": sb.failed,
-        "makespan_s": sb.makespan_s,
-        "serial": {"value": ss.throughput, "unit": UNIT, "p50_ms": 1e3 * ss.p50_s, "p99_ms": 1e3 * ss.p99_s,
-                   "makespan_s": ss.makespan_s, "failed": ss.failed},
-        "batched_over_serial": sb.throughput / ss.throughput,
-        "clocks": clk,
-        "config": {"workload": f"Poisson arrivals at {args.serve_rate:g}/s, {args.serve_requests} requests of 5/10/20 "
-                               f"CFL steps on periodic Voronoi meshes {', '.join(keys)} (nodes "
-                               f"{', '.join(str(nodes[k]) for k in keys)}), AFE N={args.order}, FP32 form, Euler",
-                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes},
-    }
-    eng.close()
-    print(json.dumps(out), flush=True)
+    t_end = 0.1
+    rows = []
+    meshes = {n: periodic_voronoi(n) for n in (8, 16, 32)}
+    for N in (2, 3):
+        for n, pm in meshes.items():
+            sub = pm.subtet_coords()
+            d = sub[:, 1:] - sub[:, :1]
+            vol_t = np.abs(np.linalg.det(d)) / 6.0
+            cell_of = np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr))
+            vol = np.bincount(cell_of, weights=vol_t, minlength=pm.n_cells)
+            finals = {}
+            for prec in (afe.AFE_FP32, afe.AFE_FP64):
+                if n == 32 and prec == afe.AFE_FP64:
+                    continue  # the FP64 form at 32^3 takes seconds per step
+                fp32 = prec == afe.AFE_FP32
+                p = afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
+                                           picard_max=128 if fp32 else 64, cfl=STABLE_CFL[N])
+                h = afe.create_from_polymesh(pm, p)
+                x = afe.afe_get_node_coords(h)
+                ptr = afe.afe_node_ptr(h, pm.n_cells)
+                afe.afe_set_state(h, states.density_wave(x))
+                dt0 = afe.afe_compute_dt(h)
+                nsteps = int(math.ceil(t_end / dt0 - 1e-9))
+                dt = t_end / nsteps
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                afe.afe_step_async(h, dt, nsteps)
+                st = afe.afe_sync(h, check=False)
+                wall = time.perf_counter() - t0
+                q = afe.afe_get_state(h)
+                afe.afe_mesh_destroy(h)
+                rho_ex = states.density_wave(x, t=t_end)[:, 0]
+                e2 = (q[:, 0] - rho_ex) ** 2
+                cnt = np.diff(ptr)
+                per_cell = np.add.reduceat(e2, ptr[:-1]) / cnt
+                l2 = float(np.sqrt(np.sum(vol * per_cell)))
+                finals[prec] = q
+                rows.append({"N": N, "n": n, "precision": "fp32" if fp32 else "fp64", "cfl": STABLE_CFL[N],
+                             "steps": nsteps, "dt": dt,
+                             "l2_rho": l2, "linf_rho": float(np.sqrt(e2.max())), "status": int(st),
+                             "ms_per_step": 1e3 * wall / nsteps, "dofs": int(5 * len(x))})
+            if len(finals) == 2:
+                a, b = finals[afe.AFE_FP32][:, 0], finals[afe.AFE_FP64][:, 0]
+                rows[-2]["rel_l2_fp32_vs_fp64"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    orders = {}
+    for N in (2, 3):
+        for prec in ("fp32", "fp64"):
+            rs = [r for r in rows if r["N"] == N and r["precision"] == prec]
+            orders[f"N{N}_{prec}"] = [math.log(r0["l2_rho"] / r1["l2_rho"]) / math.log(r1["n"] / r0["n"])
+                                      for r0, r1 in zip(rs, rs[1:])]
+    print(json.dumps({"study": "convergence", "workload": "density wave to t=0.1, periodic unit cube, "
+                                                         "CFL 0.2 (N=2) / 0.15 (N=3)",
+                      "rows": rows, "observed_order": orders}), flush=True)
 
 
 def main():
     args = _args()
+    if args.study == "convergence":
+        convergence(args)
+        return
     if args.serve:
         serve(args)
         return

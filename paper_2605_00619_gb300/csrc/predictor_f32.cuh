@@ -2,12 +2,14 @@
 //
 // One block of 512 threads per cell (persistent: blocks take cells from a work counter).
 // The cell's working set stays in shared memory for the whole fixed-point iteration:
+//   srec [S][REC]       the cell's packed sub-tet records
 //   sq   [N_i][Nt*5|1]  space-time nodal coefficients q (node-major, odd row stride)
-//   srhs [N_i][5][NTP]  right-hand side sum_k A_k^T R_k, then Y (time slices padded to a
-//                       vector width NTP: one vector load per (row, variable))
-//   sR   [CH][Nt][Np][5]  per-chunk sub-tet results R_{k,t} (deterministic gather buffer)
-//   sB   [CH][3 Np][5][NTP]  pre-contracted fluxes of the chunk's sub-tets (time innermost)
-//   sM   [NSTAGE][rows][LD] pipelined stages of M_i^-1
+//   srhs [N_i][24]      right-hand side sum_k A_k^T R_k, then Y, [5][NTP] per row (time
+//                       slices padded to a vector width NTP, columns padded to 24)
+// followed by one region used by the two phases in turn:
+//   phase 1: sR [CH][Nt][Np][5]  per-chunk sub-tet results R_{k,t} (gather buffer)
+//            sB [CH][3 Np][5][NTP]  pre-contracted fluxes of the chunk (time innermost)
+//   phase 2: ring [NSTAGE][rows][LD]  pipelined stages of M_i^-1 (as many as fit)
 // Per iteration:
 //   1. for chunks of CH sub-tets: every thread takes (sub-tet k, node j, time t) items,
 //      evaluates the flux and pre-contracts it with dt adj(J_k) (f*, g*, h*) into B; then
@@ -138,13 +140,12 @@ __host__ __device__ constexpr size_t f32_sR_bytes(int N) {
 __host__ __device__ constexpr size_t f32_sB_bytes(int N) {
   return f32_up128((size_t)f32_chunk(N) * 3 * np_of(N) * 5 * f32_ntp(N) * 4);
 }
-inline size_t f32_fixed_smem(int N, int Smax) {
-  return f32_sR_bytes(N) + f32_sB_bytes(N) + f32_up128((size_t)Smax * f32_rec_bytes(N));
-}
+// Bytes needed for the largest cell with one stage of M_i^-1.
 inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
-  auto up = [](size_t x) { return (x + 127) / 128 * 128; };
-  return f32_fixed_smem(N, Smax) + up((size_t)Nmax * f32_row_stride(N) * 4) +
-         up((size_t)Nmax * f32_rhs_stride(N) * 4) + (size_t)kF32Rows * minv_ld(Nmax) * 4;
+  const size_t phase1 = f32_sR_bytes(N) + f32_sB_bytes(N);
+  const size_t stage = (size_t)kF32Rows * minv_ld(Nmax) * 4;
+  return f32_up128((size_t)Smax * f32_rec_bytes(N)) + f32_up128((size_t)Nmax * f32_row_stride(N) * 4) +
+         f32_up128((size_t)Nmax * f32_rhs_stride(N) * 4) + std::max(phase1, stage);
 }
 
 // flux pre-contraction at one (sub-tet, time, local node j): out[d][v] = sum_e G[d][e] F_e[v]
@@ -216,14 +217,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   const int Nmax = bt.Nmax;
   auto up = [](size_t x) { return (x + 127) / 128 * 128; };
   unsigned char* p = smem_raw;
-  float* sR = (float*)p;    // [CH][NT][NP][5]
-  p += f32_sR_bytes(N);
-  float* sBc = (float*)p;   // [CH][3 NP][5][NTP]; the epilogue uses it as [warps][3][NP][5]
-  p += f32_sB_bytes(N);
   unsigned char* srec = p;  // [S][REC] sub-tet records of the current cell
   p += f32_up128((size_t)bt.Smax * REC);
-  unsigned char* const cell_base = p;  // per cell: sq [Ni][SR], srhs [Ni][SRN], M_i^-1 ring
-  float* sB = sBc + warp * 3 * NP * 5;
+  unsigned char* const cell_base = p;  // per cell: sq, srhs, then {sR, sB | M_i^-1 ring}
   (void)Nmax;
 
   for (int e = tid; e < 3 * NP * NPP; e += kF32Threads) {
@@ -276,7 +272,11 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const uint32_t* inc = m.inc + m.inc_ptr[n0];
     float* sq = reinterpret_cast<float*>(cell_base);
     float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
-    float* ring = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4));
+    unsigned char* const shared_region = cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4);
+    float* sR = reinterpret_cast<float*>(shared_region);                    // phase 1, epilogue
+    float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N));  // [CH][3 NP][5][NTP]
+    float* sB = sBc + warp * 3 * NP * 5;  // epilogue: per-warp [3][NP][5]
+    float* ring = reinterpret_cast<float*>(shared_region);                  // phase 2
     const int stage_floats = kF32Rows * LD;
     const int nstage = min(kF32MaxStages,
                            (int)(((size_t)smem_bytes - (size_t)(reinterpret_cast<unsigned char*>(ring) - smem_raw)) /
@@ -407,6 +407,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
 #pragma unroll
         for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v * NTP + t] = racc[r][v];
       }
+      // the ring reuses the phase-1 buffers: order this thread's generic-proxy accesses to
+      // them before the bulk copies (async proxy) that overwrite them
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       // ---- 2. Y = M_i^-1 RHS.  The last warp streams M_i^-1 through a ring of shared-memory
       // stages (cp.async.bulk, full/empty mbarriers); the other warps never wait for each

@@ -33,7 +33,8 @@ class Request:
     mesh: str                       # catalogue key
     nsteps: int                     # CFL steps to take
     arrival: float                  # seconds after the start of the run
-    q0: Optional[np.ndarray] = None # initial state [n_nodes, 5]; None: the engine's default
+    q0: object = None               # initial state [n_nodes, 5], a callable of the node
+                                    # coordinates [n_nodes, 3], or None (the engine's default)
     # filled in by the server
     admitted: float = math.nan
     done: float = math.nan
@@ -55,22 +56,25 @@ class Slot:
     nbytes: int
     busy: Optional[Request] = None
     remaining: int = 0
+    order: int = 0
+    xyz: Optional[np.ndarray] = None  # node coordinates (initial states given as functions)
 
 
 class GpuEngine:
     """Slot pool on the current CUDA device.
 
-    catalogue: key -> object with the arrays of ``afe_mesh_create`` (``xyz``,
-    ``cell_subtet_ptr``, ``subtet_vtx``, ``subtet_shift``, ``periodic``, ``period``).
-    slots: key -> number of slots of that mesh.  params: FP32 ``afe_params`` shared by the
-    slots.  default_state: key -> [n_nodes, 5] state used when a request brings none.
-    budget_bytes: the pool may not exceed this much device memory (None: no limit).
+    catalogue: key -> mesh (an object with the arrays of ``afe_mesh_create``: ``xyz``,
+    ``cell_subtet_ptr``, ``subtet_vtx``, ``subtet_shift``, ``periodic``, ``period``), or
+    key -> (mesh, afe_params) to give that mesh its own parameters (order, equations,
+    limiter).  slots: key -> number of slots of that mesh.  params: ``afe_params`` of the keys
+    without their own.  default_state: key -> [n_nodes, 5] state used when a request brings
+    none.  budget_bytes: the pool may not exceed this much device memory (None: no limit).
+    Batched steps need AFE_FP32 slots; slots of different orders run as one batch per order,
+    each batch on its own stream, so the groups overlap on the GPU.
     """
 
-    def __init__(self, catalogue, slots: Dict[str, int], params, default_state=None, budget_bytes=None,
+    def __init__(self, catalogue, slots: Dict[str, int], params=None, default_state=None, budget_bytes=None,
                  stream: int = 0, use_graph: bool = True, max_cached_batches: int = 16):
-        if params.precision != _afe.AFE_FP32:
-            raise ValueError("batched stepping needs AFE_FP32 parameters")
         self.params = params
         self.stream = stream
         self.use_graph = use_graph
@@ -80,34 +84,53 @@ class GpuEngine:
         self._max_cached = max_cached_batches
         total = 0
         for key, count in slots.items():
-            pm = catalogue[key]
+            entry = catalogue[key]
+            pm, prm = entry if isinstance(entry, tuple) else (entry, params)
             for _ in range(count):
-                h = _afe.create_from_polymesh(pm, params, stream)
+                h = _afe.create_from_polymesh(pm, prm, stream)
                 nb = _afe.afe_device_bytes(h)
                 if budget_bytes is not None and total + nb > budget_bytes:
                     _afe.afe_mesh_destroy(h)
                     break
                 total += nb
-                self.slots.append(Slot(len(self.slots), key, h, _afe.afe_num_nodes(h), nb))
+                self.slots.append(Slot(len(self.slots), key, h, _afe.afe_num_nodes(h), nb, order=int(prm.order),
+                                       xyz=_afe.afe_get_node_coords(h)))
         self.device_bytes = total
 
     # -- engine interface used by the server
     def load(self, slot: Slot, q0):
         q = self.default_state[slot.mesh] if q0 is None else q0
+        if callable(q):
+            q = q(slot.xyz)
         _afe.afe_set_state(slot.handle, q)
 
-    def step(self, slots: Sequence[Slot], nsteps: int) -> List[int]:
+    def _batch(self, slots: Sequence[Slot]):
         key = tuple(s.sid for s in slots)
         b = self._batches.pop(key, None)
         if b is None:
-            b = _afe.afe_batch_create([s.handle for s in slots], self.stream)
+            # a private stream per batch (stream NULL): groups of different orders overlap
+            b = _afe.afe_batch_create([s.handle for s in slots], 0)
             while len(self._batches) >= self._max_cached:
                 _, old = self._batches.popitem(last=False)
                 _afe.afe_batch_destroy(old)
         self._batches[key] = b
-        _afe.afe_batch_step_async(b, 0.0, nsteps, self.use_graph)
-        _, ms = _afe.afe_batch_sync(b, len(slots), check=False)
-        return [int(x) for x in ms]
+        return b
+
+    def step(self, slots: Sequence[Slot], nsteps: int) -> List[int]:
+        groups: Dict[int, List[int]] = {}
+        for i, s in enumerate(slots):
+            groups.setdefault(s.order, []).append(i)
+        launched = []
+        for idx in groups.values():
+            b = self._batch([slots[i] for i in idx])
+            _afe.afe_batch_step_async(b, 0.0, nsteps, self.use_graph)
+            launched.append((b, idx))
+        out = [0] * len(slots)
+        for b, idx in launched:
+            _, ms = _afe.afe_batch_sync(b, len(idx), check=False)
+            for i, st in zip(idx, ms):
+                out[i] = int(st)
+        return out
 
     def step_alone(self, slot: Slot, nsteps: int) -> int:
         _afe.afe_step_async(slot.handle, 0.0, nsteps)
