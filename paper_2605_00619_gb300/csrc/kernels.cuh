@@ -442,17 +442,17 @@ __global__ void cfl_kernel(const __grid_constant__ Batch bt) {
   const DevMesh& m = bt.tab[hh];
   const int64_t c = gc - bt.cpre[hh];
   const double mu_i = m.mu[c], kap = cell_kappa(m, mu_i), h = m.cell_h[c];
+  // per cell: lambda_v = max(4 mu / 3, kappa / c_v) / rho, weighted by 2 (2N+1) / h
+  const double gam = m.gamma, visc = fmax(4.0 * mu_i / 3.0, kap / m.cv) * (2.0 * (2 * m.N + 1) / h);
   double best = 0.0;
   bool bad = false;
   for (int64_t n = m.node_ptr[c] + lane; n < m.node_ptr[c + 1]; n += 32) {
     const double* q = m.u + n * 5;
-    const double rho = q[0];
-    const double v0 = q[1] / rho, v1 = q[2] / rho, v2 = q[3] / rho;
-    const double p = (m.gamma - 1.0) * (q[4] - 0.5 * rho * (v0 * v0 + v1 * v1 + v2 * v2));
-    const double lam = sqrt(v0 * v0 + v1 * v1 + v2 * v2) + sqrt(m.gamma * p / rho);
-    const double lv = fmax(4.0 * mu_i / (3.0 * rho), kap / (m.cv * rho));
-    double br = lam + 2.0 * lv * (2 * m.N + 1) / h;
-    if (!(br >= 0.0) || !isfinite(br)) {  // inadmissible state: report and keep dt finite
+    const double rho = q[0], ir = 1.0 / rho;  // one division per node
+    const double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const double p = (gam - 1.0) * (q[4] - 0.5 * m2 * ir);
+    double br = sqrt(m2) * ir + sqrt(gam * p * ir) + visc * ir;
+    if (!(rho > 0.0) || !(br >= 0.0) || !isfinite(br)) {  // inadmissible state: report, keep dt finite
       bad = true;
       br = 0.0;
     }

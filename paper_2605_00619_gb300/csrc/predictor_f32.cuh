@@ -398,7 +398,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             ++cur[r];
           }
         }
-        __syncthreads();
+        // no barrier here: the next chunk's flux items write only sB, and its contraction,
+        // which overwrites sR, starts after the barrier that follows those items
       }
 #pragma unroll
       for (int r = 0; r < kF32Items; ++r) {
