@@ -11,11 +11,12 @@
 //            sB [CH][3 Np][5][NTP]  pre-contracted fluxes of the chunk (time innermost)
 //   phase 2: ring [NSTAGE][rows][LD]  pipelined stages of M_i^-1 (as many as fit)
 // Per iteration:
-//   1. for chunks of CH sub-tets: every thread takes (sub-tet k, node j, time t) items,
-//      evaluates the flux and pre-contracts it with dt adj(J_k) (f*, g*, h*) into B; then
-//      every thread takes a (k, v, time pair, 4 rows m) tile of the reference-stiffness
-//      contraction R[t][m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v][t] (one float4 of S^ and
-//      one float2 of B per 8 FMAs); after the chunk each thread adds, in registers for the
+//   1. for chunks of CH sub-tets (twice as many when the cell leaves room): every thread
+//      takes (sub-tet k, node j, time t) items, evaluates the flux and pre-contracts it with
+//      dt adj(J_k) (f*, g*, h*) into B; then every thread takes a (k, v, time group, 4 rows m)
+//      tile of the reference-stiffness contraction R[t][m][v] = w_t sum_d sum_j S^_d[m][j]
+//      B_d[j][v][t] (one float4 of S^ and one float4 (wide chunks) or float2 of B per 16 or 8
+//      FMAs); after the chunk each thread adds, in registers for the
 //      nodes it owns, the chunk's incidences in (k, j) order (fixed order: the sum is
 //      bitwise reproducible and has no atomics);
 //   2. Y = M_i^-1 RHS with M_i^-1 streamed through shared memory in stages of `rows` rows by
@@ -134,12 +135,14 @@ constexpr int f32_rec_bytes(int N) { return (40 + 2 * np_of(N) + 15) / 16 * 16; 
 // takes whatever is left.  Returns the bytes needed for the largest cell with one stage.
 // Byte sizes of the fixed parts; the kernel carves its shared memory with the same functions.
 __host__ __device__ constexpr size_t f32_up128(size_t x) { return (x + 127) / 128 * 128; }
-__host__ __device__ constexpr size_t f32_sR_bytes(int N) {
-  return f32_up128((size_t)f32_chunk(N) * (N + 1) * np_of(N) * 5 * 4);
+__host__ __device__ constexpr size_t f32_sR_bytes(int N, int ch) {
+  return f32_up128((size_t)ch * (N + 1) * np_of(N) * 5 * 4);
 }
-__host__ __device__ constexpr size_t f32_sB_bytes(int N) {
-  return f32_up128((size_t)f32_chunk(N) * 3 * np_of(N) * 5 * f32_ntp(N) * 4);
+__host__ __device__ constexpr size_t f32_sB_bytes(int N, int ch) {
+  return f32_up128((size_t)ch * 3 * np_of(N) * 5 * f32_ntp(N) * 4);
 }
+__host__ __device__ constexpr size_t f32_sR_bytes(int N) { return f32_sR_bytes(N, f32_chunk(N)); }
+__host__ __device__ constexpr size_t f32_sB_bytes(int N) { return f32_sB_bytes(N, f32_chunk(N)); }
 // Bytes needed for the largest cell with one stage of M_i^-1.
 inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
   const size_t phase1 = f32_sR_bytes(N) + f32_sB_bytes(N);
@@ -273,8 +276,12 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     float* sq = reinterpret_cast<float*>(cell_base);
     float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
     unsigned char* const shared_region = cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4);
-    float* sR = reinterpret_cast<float*>(shared_region);                    // phase 1, epilogue
-    float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N));  // [CH][3 NP][5][NTP]
+    // chunks of 2 CH sub-tets (4-time contraction tiles) when the cell leaves room for them
+    const size_t region_bytes = (size_t)smem_bytes - (size_t)(shared_region - smem_raw);
+    const bool wide = NTP == 4 && region_bytes >= f32_sR_bytes(N, 2 * CH) + f32_sB_bytes(N, 2 * CH);
+    const int CHc = wide ? 2 * CH : CH;
+    float* sR = reinterpret_cast<float*>(shared_region);                          // phase 1, epilogue
+    float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc][3 NP][5][NTP]
     float* sB = sBc + warp * 3 * NP * 5;  // epilogue: per-warp [3][NP][5]
     float* ring = reinterpret_cast<float*>(shared_region);                  // phase 2
     const int stage_floats = kF32Rows * LD;
@@ -342,64 +349,89 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           cend[r] = (int)(m.inc_ptr[n0 + inode[r] + 1] - m.inc_ptr[n0]);
         }
       }
-      for (int kc = 0; kc < S; kc += CH) {
-        const int nk = min(CH, S - kc);
-        // (a) fluxes: items (k, j, t), t fastest (conflict-free stores into B)
-        for (int e = tid; e < nk * NP * NT; e += kF32Threads) {
-          const int t = e % NT, j = (e / NT) % NP, kl = e / (NT * NP);
-          float out[3][5];
-          f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt, sD, out);
-          float* dst = sBc + ((size_t)(kl * 3 * NP + j) * 5) * NTP + t;
+      // one chunk size per instantiation: CHT sub-tets, contraction tiles of TW time slices
+      auto phase1 = [&](auto chunk_tag) {
+        constexpr int CHT = decltype(chunk_tag)::value;
+        constexpr int TW = (CHT > CH) ? 4 : 2;  // 4 x 4 tiles for wide chunks, 4 x 2 otherwise
+        constexpr int TGN = NTP / TW;           // time groups per tile column
+        for (int kc = 0; kc < S; kc += CHT) {
+          const int nk = min(CHT, S - kc);
+          // (a) fluxes: items (k, j, t), t fastest (conflict-free stores into B)
+          for (int e = tid; e < nk * NP * NT; e += kF32Threads) {
+            const int t = e % NT, j = (e / NT) % NP, kl = e / (NT * NP);
+            float out[3][5];
+            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt, sD, out);
+            float* dst = sBc + ((size_t)(kl * 3 * NP + j) * 5) * NTP + t;
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
+            for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) dst[(d * NP * 5 + v) * NTP] = out[d][v];
-        }
-        __syncthreads();
-        // (b) R[k][t][m][v] = w_t sum_{d,j} S^_d[m][j] B[k][d j][v][t]: tile (k, v, time pair,
-        // rows 4mg..4mg+3), mg fastest
-        for (int e = tid; e < nk * 5 * TPN * MG; e += kF32Threads) {
-          const int mg = e % MG, tp = (e / MG) % TPN, v = (e / (MG * TPN)) % 5, kl = e / (MG * TPN * 5);
-          float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-          const float* bcol = sBc + ((size_t)kl * 3 * NP * 5 + v) * NTP + 2 * tp;
-          const float* scol = &sSt[0][0][4 * mg];
+              for (int v = 0; v < 5; ++v) dst[(d * NP * 5 + v) * NTP] = out[d][v];
+          }
+          __syncthreads();
+          // (b) R[k][t][m][v] = w_t sum_{d,j} S^_d[m][j] B[k][d j][v][t]: tile (k, v, time group,
+          // rows 4mg..4mg+3), mg fastest; one float4 of S^ and one TW-vector of B per 4 TW FMAs
+          for (int e = tid; e < nk * 5 * TGN * MG; e += kF32Threads) {
+            const int mg = e % MG, tg = (e / MG) % TGN, v = (e / (MG * TGN)) % 5, kl = e / (MG * TGN * 5);
+            float acc[TW][4];
+#pragma unroll
+            for (int h = 0; h < TW; ++h)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) acc[h][i] = 0.f;
+            const float* bcol = sBc + ((size_t)kl * 3 * NP * 5 + v) * NTP + TW * tg;
+            const float* scol = &sSt[0][0][4 * mg];
 #pragma unroll 6
-          for (int kk = 0; kk < 3 * NP; ++kk) {
-            const float4 s4 = *reinterpret_cast<const float4*>(scol + kk * NPP);
-            const float2 b2 = *reinterpret_cast<const float2*>(bcol + kk * 5 * NTP);
-            a0[0] += s4.x * b2.x; a0[1] += s4.y * b2.x; a0[2] += s4.z * b2.x; a0[3] += s4.w * b2.x;
-            a1[0] += s4.x * b2.y; a1[1] += s4.y * b2.y; a1[2] += s4.z * b2.y; a1[3] += s4.w * b2.y;
-          }
+            for (int kk = 0; kk < 3 * NP; ++kk) {
+              const float4 s4 = *reinterpret_cast<const float4*>(scol + kk * NPP);
+              float bv[TW];
+              if constexpr (TW == 4) {
+                const float4 b4 = *reinterpret_cast<const float4*>(bcol + kk * 5 * NTP);
+                bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
+              } else {
+                const float2 b2 = *reinterpret_cast<const float2*>(bcol + kk * 5 * NTP);
+                bv[0] = b2.x; bv[1] = b2.y;
+              }
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int t = 2 * tp + h;
-            if (t >= NT) continue;
-            const float wt = sW[t];
-            float* dst = sR + ((kl * NT + t) * NP + 4 * mg) * 5 + v;
-            const float* av = h == 0 ? a0 : a1;
+              for (int h = 0; h < TW; ++h) {
+                acc[h][0] += s4.x * bv[h]; acc[h][1] += s4.y * bv[h];
+                acc[h][2] += s4.z * bv[h]; acc[h][3] += s4.w * bv[h];
+              }
+            }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              if (4 * mg + i < NP) dst[5 * i] = wt * av[i];
+            for (int h = 0; h < TW; ++h) {
+              const int t = TW * tg + h;
+              if (t >= NT) continue;
+              const float wt = sW[t];
+              float* dst = sR + ((kl * NT + t) * NP + 4 * mg) * 5 + v;
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                if (4 * mg + i < NP) dst[5 * i] = wt * acc[h][i];
+            }
           }
+          __syncthreads();
+          // gather this chunk's incidences, in (k, j) order, into the items' registers
+#pragma unroll
+          for (int r = 0; r < kF32Items; ++r) {
+            if (inode[r] < 0) continue;
+            const int t = (tid + r * kF32Threads) % NT;
+            while (cur[r] < cend[r]) {
+              const uint32_t w = inc[cur[r]];
+              const int k = (int)(w >> 5) - kc;
+              if (k >= nk) break;
+              const float* src = sR + ((k * NT + t) * NP + (int)(w & 31)) * 5;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) racc[r][v] += src[v];
+              ++cur[r];
+            }
+          }
+          // no barrier here: the next chunk's flux items write only sB, and its contraction,
+          // which overwrites sR, starts after the barrier that follows those items
         }
-        __syncthreads();
-        // gather this chunk's incidences, in (k, j) order, into the items' registers
-#pragma unroll
-        for (int r = 0; r < kF32Items; ++r) {
-          if (inode[r] < 0) continue;
-          const int t = (tid + r * kF32Threads) % NT;
-          while (cur[r] < cend[r]) {
-            const uint32_t w = inc[cur[r]];
-            const int k = (int)(w >> 5) - kc;
-            if (k >= nk) break;
-            const float* src = sR + ((k * NT + t) * NP + (int)(w & 31)) * 5;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) racc[r][v] += src[v];
-            ++cur[r];
-          }
-        }
-        // no barrier here: the next chunk's flux items write only sB, and its contraction,
-        // which overwrites sR, starts after the barrier that follows those items
+      };
+      if constexpr (NTP == 4) {
+        if (wide) phase1(std::integral_constant<int, 2 * CH>{});
+        else phase1(std::integral_constant<int, CH>{});
+      } else {
+        phase1(std::integral_constant<int, CH>{});
       }
 #pragma unroll
       for (int r = 0; r < kF32Items; ++r) {
@@ -617,7 +649,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         vend[r] = (int)(m.inc_ptr[n0 + n + 1] - m.inc_ptr[n0]);
       }
     }
-    const int CHV = CH * NT;  // sub-tets per volume chunk (sR holds CH*NT slices)
+    const int CHV = CHc * NT;  // sub-tets per volume chunk (sR holds CHc*NT slices)
     for (int kc = 0; kc < S; kc += CHV) {
       const int nk = min(CHV, S - kc);
       for (int kl = warp; kl < nk; kl += kF32Warps) {
