@@ -363,7 +363,7 @@ def ours(args):
             for _ in range(steps):
                 afe.afe_set_state(h, hin)
                 afe.afe_step(h, 0.0, check=False)
-                hin[:] = afe.afe_get_state(h)
+                afe.afe_get_state(h, out=hin)
             barrier()
             rec["e2e_wall"] = time.perf_counter() - t1
         afe.afe_mesh_destroy(h)

@@ -215,8 +215,11 @@ def afe_set_state_device(m, dptr: int, stream: int = 0):
     _check(lib().afe_set_state_device(m, _P(dptr), _P(stream)))
 
 
-def afe_get_state(m):
-    q = np.empty((afe_num_nodes(m), 5), np.float64)
+def afe_get_state(m, out=None):
+    """State [n_nodes, 5] into ``out`` (C-contiguous float64, e.g. pinned host memory) or a new array."""
+    q = np.empty((afe_num_nodes(m), 5), np.float64) if out is None else out
+    if q.dtype != np.float64 or not q.flags.c_contiguous or q.shape != (afe_num_nodes(m), 5):
+        raise ValueError("out must be a C-contiguous float64 array of shape [n_nodes, 5]")
     _check(lib().afe_get_state(m, _dptr(q)))
     return q
 

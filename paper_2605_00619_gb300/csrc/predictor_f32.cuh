@@ -41,7 +41,7 @@ namespace afe {
 
 constexpr int kF32Threads = 512;
 constexpr int kF32Warps = kF32Threads / 32;
-constexpr int kF32Rows = 16;     // rows of M_i^-1 per pipeline stage
+constexpr int kF32Rows = 32;     // rows of M_i^-1 per pipeline stage
 constexpr int kF32MaxStages = 8;
 constexpr int kF32Consumers = kF32Warps - 1;  // warps that apply M_i^-1 (the last one loads it)
 
