@@ -144,11 +144,17 @@ __host__ __device__ constexpr size_t f32_sB_bytes(int N, int ch) {
 __host__ __device__ constexpr size_t f32_sR_bytes(int N) { return f32_sR_bytes(N, f32_chunk(N)); }
 __host__ __device__ constexpr size_t f32_sB_bytes(int N) { return f32_sB_bytes(N, f32_chunk(N)); }
 // Bytes needed for the largest cell with one stage of M_i^-1.
+// The cell's node -> (sub-tet, local node) incidences (one per sub-tet node) and their row
+// offsets, staged in shared memory for the gathers.
+__host__ __device__ constexpr size_t f32_inc_bytes(int N, int Smax) {
+  return f32_up128((size_t)Smax * np_of(N) * 4) + f32_up128((size_t)(kF32MaxNodes + 1) * 4);
+}
 inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
   const size_t phase1 = f32_sR_bytes(N) + f32_sB_bytes(N);
   const size_t stage = (size_t)kF32Rows * minv_ld(Nmax) * 4;
-  return f32_up128((size_t)Smax * f32_rec_bytes(N)) + f32_up128((size_t)Nmax * f32_row_stride(N) * 4) +
-         f32_up128((size_t)Nmax * f32_rhs_stride(N) * 4) + std::max(phase1, stage);
+  return f32_up128((size_t)Smax * f32_rec_bytes(N)) + f32_inc_bytes(N, Smax) +
+         f32_up128((size_t)Nmax * f32_row_stride(N) * 4) + f32_up128((size_t)Nmax * f32_rhs_stride(N) * 4) +
+         std::max(phase1, stage);
 }
 
 // flux pre-contraction at one (sub-tet, time, local node j): out[d][v] = sum_e G[d][e] F_e[v]
@@ -222,6 +228,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   unsigned char* p = smem_raw;
   unsigned char* srec = p;  // [S][REC] sub-tet records of the current cell
   p += f32_up128((size_t)bt.Smax * REC);
+  uint32_t* sinc = reinterpret_cast<uint32_t*>(p);  // [incidences] (k << 5) | j of the cell's nodes
+  int* sincp = reinterpret_cast<int*>(p + f32_up128((size_t)bt.Smax * NP * 4));  // [N_i + 1] row offsets
+  p += f32_inc_bytes(N, bt.Smax);
   unsigned char* const cell_base = p;  // per cell: sq, srhs, then {sR, sB | M_i^-1 ring}
   (void)Nmax;
 
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const float kap = (float)cell_kappa(m, m.mu[c]);
     const bool visc = (mu != 0.f) || (kap != 0.f);
     const float* minv = m.minv32 + m.minv_ptr[c];
-    const uint32_t* inc = m.inc + m.inc_ptr[n0];
+    const uint32_t* inc = sinc;  // the cell's incidences, staged in shared memory below
     float* sq = reinterpret_cast<float*>(cell_base);
     float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
     unsigned char* const shared_region = cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4);
@@ -310,6 +319,12 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     }
     // the padded columns of RHS stay zero (so do those of Y)
     for (int e = tid; e < Ni * SRN; e += kF32Threads) srhs[e] = 0.f;
+    {
+      const int64_t ib = m.inc_ptr[n0];
+      const int ninc = (int)(m.inc_ptr[n0 + Ni] - ib);  // <= S * NP
+      for (int e = tid; e < ninc; e += kF32Threads) sinc[e] = m.inc[ib + e];
+      for (int e = tid; e <= Ni; e += kF32Threads) sincp[e] = (int)(m.inc_ptr[n0 + e] - ib);
+    }
     if (tid == 0 && !mbar_wait_bounded(&sbar, phase & 1u)) {
       atomicOr(&m.flags[F_TIMEOUT], 1);
       sAbort = 1;
@@ -345,8 +360,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
 #pragma unroll
         for (int v = 0; v < 5; ++v) racc[r][v] = 0.f;
         if (inode[r] >= 0) {
-          cur[r] = (int)(m.inc_ptr[n0 + inode[r]] - m.inc_ptr[n0]);
-          cend[r] = (int)(m.inc_ptr[n0 + inode[r] + 1] - m.inc_ptr[n0]);
+          cur[r] = sincp[inode[r]];
+          cend[r] = sincp[inode[r] + 1];
         }
       }
       // one chunk size per instantiation: CHT sub-tets, contraction tiles of TW time slices
@@ -645,8 +660,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       for (int v = 0; v < 5; ++v) vacc[r][v] = 0.f;
       vcur[r] = vend[r] = 0;
       if (n < Ni) {
-        vcur[r] = (int)(m.inc_ptr[n0 + n] - m.inc_ptr[n0]);
-        vend[r] = (int)(m.inc_ptr[n0 + n + 1] - m.inc_ptr[n0]);
+        vcur[r] = sincp[n];
+        vend[r] = sincp[n + 1];
       }
     }
     const int CHV = CHc * NT;  // sub-tets per volume chunk (sR holds CHc*NT slices)
