@@ -95,6 +95,42 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// acc[v] += rows[(k - kc) row of incidence][v] over the incidences inc[cur .. end) whose
+// sub-tet k lies in [kc, kc + nk), in list order (the list is sorted by k).  Four incidences
+// are fetched per round so that their shared-memory loads overlap; the additions keep the
+// list order, so the sum is the same as one incidence at a time.
+template <typename RowOf>
+__device__ __forceinline__ void gather_in_order(const uint32_t* __restrict__ inc, int& cur, int end, int kc,
+                                                int nk, RowOf row_of, float (&acc)[5]) {
+  while (cur < end) {
+    bool ok[4];
+    const float* src[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ok[q] = cur + q < end;
+      const uint32_t w = ok[q] ? inc[cur + q] : 0u;
+      const int k = (int)(w >> 5) - kc;
+      ok[q] = ok[q] && k < nk;  // a prefix of the four (the list is sorted by k)
+      src[q] = row_of(ok[q] ? k : 0, (int)(w & 31));
+    }
+    float val[4][5];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) val[q][v] = ok[q] ? src[q][v] : 0.f;
+    int adv = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (ok[q]) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc[v] += val[q][v];
+        ++adv;
+      }
+    cur += adv;
+    if (adv < 4) break;
+  }
+}
+
 // Bulk (TMA) copy of `bytes` (multiple of 16, both addresses 16-byte aligned) global -> shared,
 // completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -428,15 +464,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           for (int r = 0; r < kF32Items; ++r) {
             if (inode[r] < 0) continue;
             const int t = (tid + r * kF32Threads) % NT;
-            while (cur[r] < cend[r]) {
-              const uint32_t w = inc[cur[r]];
-              const int k = (int)(w >> 5) - kc;
-              if (k >= nk) break;
-              const float* src = sR + ((k * NT + t) * NP + (int)(w & 31)) * 5;
-#pragma unroll
-              for (int v = 0; v < 5; ++v) racc[r][v] += src[v];
-              ++cur[r];
-            }
+            gather_in_order(inc, cur[r], cend[r], kc, nk,
+                            [&](int k, int j) { return sR + ((k * NT + t) * NP + j) * 5; }, racc[r]);
           }
           // no barrier here: the next chunk's flux items write only sB, and its contraction,
           // which overwrites sR, starts after the barrier that follows those items
@@ -710,15 +739,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        while (vcur[r] < vend[r]) {
-          const uint32_t w = inc[vcur[r]];
-          const int k = (int)(w >> 5) - kc;
-          if (k >= nk) break;
-          const float* src = sR + (k * NP + (int)(w & 31)) * 5;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) vacc[r][v] += src[v];
-          ++vcur[r];
-        }
+        gather_in_order(inc, vcur[r], vend[r], kc, nk, [&](int k, int j) { return sR + (k * NP + j) * 5; },
+                        vacc[r]);
       }
       __syncthreads();
     }
