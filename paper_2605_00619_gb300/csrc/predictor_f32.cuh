@@ -242,12 +242,12 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), SR = f32_row_stride(N);
   constexpr int NTP = f32_ntp(N), SRN = f32_rhs_stride(N), CH = f32_chunk(N);
   constexpr int NPP = (NP + 3) / 4 * 4;  // rows of sSt padded to 16 bytes
-  constexpr int MG = NPP / 4, TPN = NTP / 2;  // 4-row groups of R, time-slice pairs
-  static_assert(CH * 3 * NP * 5 * NTP >= kF32Warps * 3 * NP * 5, "epilogue staging must fit in sB");
+  constexpr int MG = NPP / 4;  // 4-row groups of R
+  static_assert(NTP >= NT, "the epilogue's [CH NT][3 NP][5] staging must fit in sB");
   constexpr int REC = f32_rec_bytes(N);  // bytes per sub-tet record
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(16) float sSt[3][NP][NPP];  // sSt[d][j][m] = S^_d[m][j] (zero padded)
-  __shared__ float sSo[3][NP][NP];   // sSo[d][j][m] = S^_d[j][m]  (volume term, lane = m)
+  __shared__ __align__(16) float sSo[3][NP][NPP];  // sSo[d][j][m] = S^_d[j][m] (volume term, zero padded)
   __shared__ float sD[3][NP][NP];    // nodal derivative matrices (viscous fluxes)
   __shared__ float sK[NT][NT];
   __shared__ float sW[NT];
@@ -278,6 +278,10 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const int d = e / (NP * NP), r = (e / NP) % NP, c = e % NP;
     sSo[d][r][c] = (float)ref->S[d][r][c];
     sD[d][r][c] = (float)ref->D[d][r][c];
+  }
+  if constexpr (NPP > NP) {  // zero padding columns of sSo
+    constexpr int PAD = NPP > NP ? NPP - NP : 1;
+    for (int e = tid; e < 3 * NP * PAD; e += kF32Threads) sSo[e / (NP * PAD)][(e / PAD) % NP][NP + e % PAD] = 0.f;
   }
   if (tid < NT * NT) sK[tid / NT][tid % NT] = (float)ref->K1tinv[tid / NT][tid % NT];
   if (tid < NT) sW[tid] = (float)ref->w[tid];
@@ -327,7 +331,6 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const int CHc = wide ? 2 * CH : CH;
     float* sR = reinterpret_cast<float*>(shared_region);                          // phase 1, epilogue
     float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc][3 NP][5][NTP]
-    float* sB = sBc + warp * 3 * NP * 5;  // epilogue: per-warp [3][NP][5]
     float* ring = reinterpret_cast<float*>(shared_region);                  // phase 2
     const int stage_floats = kF32Rows * LD;
     const int nstage = min(kF32MaxStages,
@@ -694,47 +697,61 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       }
     }
     const int CHV = CHc * NT;  // sub-tets per volume chunk (sR holds CHc*NT slices)
+    float* sBv = sBc;          // [CHV][3 NP][5] time-integrated pre-contracted fluxes (fits in sB)
     for (int kc = 0; kc < S; kc += CHV) {
       const int nk = min(CHV, S - kc);
-      for (int kl = warp; kl < nk; kl += kF32Warps) {
-        const float* g = rec_g(kc + kl);
-        const uint16_t* Ak = rec_a(kc + kl);
-        if (lane < NP) {
-          float accb[3][5];
+      // (a) items (k, j): B_bar[k][d j][v] = sum_t w_t dt adj(J_k) F(q_t) at node j
+      for (int e = tid; e < nk * NP; e += kF32Threads) {
+        const int kl = e / NP, j = e % NP;
+        float accb[3][5];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) accb[d][v] = 0.f;
+        for (int t = 0; t < NT; ++t) {
+          float out[3][5];
+          f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt * sW[t], sD,
+                               out);
 #pragma unroll
           for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) accb[d][v] = 0.f;
-          for (int t = 0; t < NT; ++t) {
-            float out[3][5];
-            f32_flux_contract<N>(sq, Ak, g, lane, t, visc, mu, kap, gam, Rg, dt * sW[t], sD, out);
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-              for (int v = 0; v < 5; ++v) accb[d][v] += out[d][v];
-          }
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int v = 0; v < 5; ++v) sB[(d * NP + lane) * 5 + v] = accb[d][v];
+            for (int v = 0; v < 5; ++v) accb[d][v] += out[d][v];
         }
-        __syncwarp();
-        if (lane < NP) {
-          float a5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float* dst = sBv + ((size_t)kl * 3 * NP + j) * 5;
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dst[d * NP * 5 + v] = accb[d][v];
+      }
+      __syncthreads();
+      // (b) R_bar[k][m][v] = sum_{d,j} S^_d[j][m] B_bar[k][d j][v]: tile (k, rows 4mg..4mg+3, all v)
+      for (int e = tid; e < nk * MG; e += kF32Threads) {
+        const int kl = e / MG, mg = e % MG;
+        float acc[4][5];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) acc[i][v] = 0.f;
+        const float* bk = sBv + (size_t)kl * 3 * NP * 5;
+        const float* scol = &sSo[0][0][4 * mg];
 #pragma unroll 4
-            for (int j = 0; j < NP; ++j) {
-              const float sv = sSo[d][j][lane];
-              const float* b = sB + (d * NP + j) * 5;
+        for (int kk = 0; kk < 3 * NP; ++kk) {
+          const float4 s4 = *reinterpret_cast<const float4*>(scol + kk * NPP);
+          const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-              for (int v = 0; v < 5; ++v) a5[v] += sv * b[v];
-            }
-          float* dst = sR + (kl * NP + lane) * 5;
+          for (int v = 0; v < 5; ++v) {
+            const float b = bk[kk * 5 + v];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) dst[v] = a5[v];
+            for (int i = 0; i < 4; ++i) acc[i][v] += sv[i] * b;
+          }
         }
-        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (4 * mg + i < NP) {
+            float* dst = sR + (kl * NP + 4 * mg + i) * 5;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) dst[v] = acc[i][v];
+          }
       }
       __syncthreads();
 #pragma unroll
@@ -742,8 +759,10 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         gather_in_order(inc, vcur[r], vend[r], kc, nk, [&](int k, int j) { return sR + (k * NP + j) * 5; },
                         vacc[r]);
       }
-      __syncthreads();
+      // no barrier here: the next chunk's items write only B_bar, and its tiles, which
+      // overwrite sR, start after the barrier that follows those items
     }
+    __syncthreads();
     float* vol = (float*)m.vol;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
