@@ -142,3 +142,32 @@ def test_serving_loop_results_equal_alone(afe, meshes):
     for h in solo.values():
         afe.afe_mesh_destroy(h)
     eng.close()
+
+
+def test_graph_recaptured_when_dt_changes(afe, meshes):
+    """A fixed dt, then the CFL step, then another fixed dt through one batch: the graph is
+    re-captured at each change and every member still equals stepping it alone."""
+    allm = _members(afe, meshes)
+    mem = allm[:2]
+    plan = [(0.0005, 2), (0.0, 2), (0.00025, 1)]
+    ref = []
+    for h, u0 in mem:
+        afe.afe_set_state(h, u0)
+        for dt, n in plan:
+            afe.afe_step_async(h, dt, n)
+        assert afe.afe_sync(h, check=False) in (0, 5)
+        ref.append(afe.afe_get_state(h))
+    for h, u0 in mem:
+        afe.afe_set_state(h, u0)
+    b = afe.afe_batch_create([h for h, _ in mem])
+    for dt, n in plan:
+        afe.afe_batch_step_async(b, dt, n, True)
+    afe.afe_batch_sync(b, len(mem), check=False)
+    cells, nodes, launches, graphs = afe.afe_batch_info(b)
+    afe.afe_batch_destroy(b)
+    assert graphs == sum(n for _, n in plan)
+    assert nodes == sum(afe.afe_num_nodes(h) for h, _ in mem)
+    for (h, _), q in zip(mem, ref):
+        np.testing.assert_array_equal(afe.afe_get_state(h), q)
+    for h, _ in allm:
+        afe.afe_mesh_destroy(h)

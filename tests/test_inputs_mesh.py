@@ -87,3 +87,19 @@ def test_collapse_removes_short_edges():
     raw = V.periodic_voronoi(4, collapse=0.0)
     Xr = raw.subtet_coords()
     assert np.linalg.norm(Xr[:, 3] - Xr[:, 2], axis=1).min() < edge.min()
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_quality_step_leaves_no_degenerate_sub_tets(n):
+    """After the Lloyd steps and the collapse (with its fold retry) no sub-tet is a needle:
+    every edge of the fan is longer than 0.15 lattice spacings and every sub-tet holds at
+    least 2 % of its cell's mean sub-tet volume."""
+    pm = V.periodic_voronoi(n)
+    P = pm.subtet_coords()
+    h = 1.0 / n
+    edge = np.linalg.norm(P[:, 3] - P[:, 2], axis=1) / h
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6.0
+    cell = np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr))
+    mean = np.bincount(cell, weights=vol) / np.bincount(cell)
+    assert edge.min() > 0.15
+    assert (vol / mean[cell]).min() > 0.02
