@@ -814,6 +814,10 @@ __global__ void face_kernel(const __grid_constant__ Batch bt) {
   const double mu_i = m.mu[ci], kap_i = cell_kappa(m, mu_i);
   const double mu_j = cj >= 0 ? m.mu[cj] : mu_i, kap_j = cell_kappa(m, mu_j);
   const double h_i = m.cell_h[ci], h_j = cj >= 0 ? m.cell_h[cj] : h_i;
+  // |lambda_v| = max(4 mu / 3, kappa / c_v) / rho: the coefficient once per side, then one
+  // reciprocal per face node (1 / rho = dt / q_bar_rho)
+  const Real cvis_i = (Real)fmax(4.0 * mu_i / 3.0, kap_i / m.cv), cvis_j = (Real)fmax(4.0 * mu_j / 3.0, kap_j / m.cv);
+  const Real rdt = (Real)dt;
   Real smax = 0, vmax = 0;
   for (int e = lane; e < nitems; e += 32) {
     const int64_t s = m.group_slot[g0 + e / NF];
@@ -829,9 +833,9 @@ __global__ void face_kernel(const __grid_constant__ Batch bt) {
       const Real v0 = Q[1] * ir, v1 = Q[2] * ir, v2 = Q[3] * ir;  // q_bar / dt ratios
       const Real p = (gam - 1) * (Q[4] * idt - Real(0.5) * rho * (v0 * v0 + v1 * v1 + v2 * v2));
       const Real vn = fabs(v0 * (Real)g[0] + v1 * (Real)g[1] + v2 * (Real)g[2]);
-      smax = fmax(smax, vn + sqrt(gam * p / rho));
-      const double mus = side == 0 ? mu_i : mu_j, kps = side == 0 ? kap_i : kap_j;
-      vmax = fmax(vmax, (Real)fmax(4.0 * mus / (3.0 * (double)rho), kps / (m.cv * (double)rho)));
+      const Real irho = ir * rdt;  // 1 / rho
+      smax = fmax(smax, vn + sqrt(gam * p * irho));
+      vmax = fmax(vmax, (side == 0 ? cvis_i : cvis_j) * irho);
     }
   }
 #pragma unroll
