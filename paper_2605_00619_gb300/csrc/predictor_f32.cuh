@@ -1003,9 +1003,10 @@ __global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __gri
         un[v] += (double)du[r][i][v] + corr[v];
         bad |= !isfinite(un[v]);
       }
+      // rho > 0 and p > 0, with p > 0 tested as rho E > |rho u|^2 / 2 (no division)
       const double rho = un[0];
-      const double p = (m.gamma - 1.0) * (un[4] - 0.5 * (un[1] * un[1] + un[2] * un[2] + un[3] * un[3]) / rho);
-      if (bad || !(rho > 0.0) || !(p > 0.0)) atomicOr(&m.flags[F_NONFINITE], 8);
+      const double pr = rho * un[4] - 0.5 * (un[1] * un[1] + un[2] * un[2] + un[3] * un[3]);
+      if (bad || !(rho > 0.0) || !(pr > 0.0)) atomicOr(&m.flags[F_NONFINITE], 8);
     }
   }
 }
