@@ -39,10 +39,10 @@ METRIC = "DOF-updates/s per ADER-DG step"
 STABLE_CFL = {1: 0.3, 2: 0.2, 3: 0.15}
 
 # DRAM bytes (read + write) of one predictor_f32_kernel<3> launch per cell, from the ncu
-# capture summarised in profiles/step_kernels_density_wave_12c_N3.md (905 MB over 1728 cells
+# capture summarised in profiles/step_kernels_density_wave_12c_N3.md (907 MB over 1728 cells
 # of the density-wave workload): the fixed-point iterations re-read M_i^-1 from L2, so the
 # traffic grows with the cells, not with the iterations.  Valid for that kernel version only.
-PREDICTOR_N3_DRAM_BYTES_PER_CELL = (863.081472e6 + 41.609984e6) / 1728
+PREDICTOR_N3_DRAM_BYTES_PER_CELL = (865.222656e6 + 42.158848e6) / 1728
 UNIT = "DOF-updates/s"
 
 
