@@ -59,8 +59,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cfl", type=float, default=None,
                     help="CFL number (default: 0.3, the paper's, for the density wave; the stable one otherwise)")
+    ap.add_argument("--visc-dt", default="subtet", choices=["subtet", "cell"],
+                    help="shock/tgv: length in the viscous term of the time step (the smallest "
+                         "sub-tet length, or the cell length as printed; see the stokes study)")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
-    ap.add_argument("--study", choices=["convergence"], help="accuracy study instead of the throughput run")
+    ap.add_argument("--study", choices=["convergence", "stokes"], help="accuracy study instead of the throughput run")
     ap.add_argument("--workload", default="density", choices=["density", "shock", "tgv"],
                     help="density: density wave, periodic unit cube, Euler; shock: spherical explosion on "
                          "[-1,1]^3, transmissive, limiter on; tgv: Navier-Stokes Taylor-Green vortex on "
@@ -308,7 +311,10 @@ def ours(args):
         if args.workload == "shock":
             extra = dict(limiter=1)
         elif args.workload == "tgv":
-            extra = dict(equations=afe.AFE_NAVIER_STOKES, mu=0.01, Pr=0.71, kappa=-1.0)
+            extra = dict(equations=afe.AFE_NAVIER_STOKES, mu=0.01, Pr=0.71, kappa=-1.0,
+                         visc_dt_subtet=int(args.visc_dt == "subtet"))
+        if args.workload == "shock":
+            extra["visc_dt_subtet"] = int(args.visc_dt == "subtet")
         p = afe.afe_default_params(args.order, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
                                    picard_max=128 if fp32 else 64, cfl=cfl, **extra)
         h = afe.create_from_polymesh(pm, p, stream=sid)
@@ -384,7 +390,9 @@ def ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(args.n, args.order, args.workload), "cells": pm.n_cells, "nodes": r32["n_nodes"],
+        "config": {"workload": workload_name(args.n, args.order, args.workload)
+                   + (f", viscous time step from the {args.visc_dt} length" if args.workload != "density" else ""),
+                   "cells": pm.n_cells, "nodes": r32["n_nodes"],
                    "dofs": dofs, "precision": "FP32 arithmetic, FP64 master state / dt / cell totals",
                    "picard_tol": 1e-6, "l2": "inputs larger than L2 (M_i^-1 alone is "
                    f"{r32['bytes'] / 1e9:.1f} GB of device state)", "parallelism": f"{world} independent replicas"},
@@ -575,7 +583,7 @@ def convergence(args):
             vol = np.bincount(cell_of, weights=vol_t, minlength=pm.n_cells)
             finals = {}
             for prec in (afe.AFE_FP32, afe.AFE_FP64):
-                if n == 32 and prec == afe.AFE_FP64:
+                if n == 32 and (prec == afe.AFE_FP64 or N > 1):
                     continue  # the FP64 form at 32^3 takes seconds per step
                 fp32 = prec == afe.AFE_FP32
                 p = afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
@@ -618,10 +626,75 @@ def convergence(args):
                       "rows": rows, "observed_order": orders}), flush=True)
 
 
+def stokes(args):
+    """Viscous check: periodic form of the first problem of Stokes (two shear layers, nu = mu =
+    1e-3 with rho = 1, p = 1/gamma, Navier-Stokes, kappa from Pr 0.71), integrated to t = 0.25
+    on periodic meshes of 8^3 and 16^3 cells (N = 1, 2; FP32 and FP64 forms) and 32^3 cells
+    (N = 1, FP32) at the stable CFL, with the viscous term of the time step bounded by the
+    smallest sub-tet length (with the cell length, as printed, these runs go non-finite
+    within 20 steps).  One JSON line per run, then a summary line.
+    Reported: the volume-weighted nodal L2 error of the shear velocity v against the closed
+    form v = erf profiles of width 2 sqrt(nu (t + 0.05)), and the status.
+    """
+    import numpy as np
+    import torch
+
+    from inputs import states
+    from inputs.voronoi import periodic_voronoi
+    from paper_2605_00619_gb300 import afe
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    afe.lib()
+    nu, t_end = 1e-3, 0.25
+    rows = []
+    for n in (8, 16, 32):
+        pm = periodic_voronoi(n)
+        sub = pm.subtet_coords()
+        vol_t = np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0
+        cell_of = np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr))
+        vol = np.bincount(cell_of, weights=vol_t, minlength=pm.n_cells)
+        for N in (1, 2):
+            for prec in (afe.AFE_FP32, afe.AFE_FP64):
+                if n == 32 and (prec == afe.AFE_FP64 or N > 1):
+                    continue
+                fp32 = prec == afe.AFE_FP32
+                p = afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
+                                           picard_max=128 if fp32 else 64, cfl=STABLE_CFL[N],
+                                           equations=afe.AFE_NAVIER_STOKES, mu=nu, Pr=0.71, kappa=-1.0,
+                                           visc_dt_subtet=1)
+                h = afe.create_from_polymesh(pm, p)
+                x = afe.afe_get_node_coords(h)
+                ptr = afe.afe_node_ptr(h, pm.n_cells)
+                afe.afe_set_state(h, states.shear_layers(x, nu))
+                dt0 = afe.afe_compute_dt(h)
+                nsteps = int(math.ceil(t_end / dt0 - 1e-9))
+                dt = t_end / nsteps
+                t0 = time.perf_counter()
+                afe.afe_step_async(h, dt, nsteps)
+                st = afe.afe_sync(h, check=False)
+                wall = time.perf_counter() - t0
+                q = afe.afe_get_state(h)
+                afe.afe_mesh_destroy(h)
+                v = q[:, 2] / q[:, 0]
+                v_ex = states.shear_layers(x, nu, t=t_end)[:, 2]
+                e2 = (v - v_ex) ** 2
+                per_cell = np.add.reduceat(e2, ptr[:-1]) / np.diff(ptr)
+                rows.append({"n": n, "N": N, "precision": "fp32" if fp32 else "fp64", "steps": nsteps, "dt": dt,
+                             "l2_v": float(np.sqrt(np.sum(vol * per_cell))), "linf_v": float(np.sqrt(e2.max())),
+                             "status": int(st), "ms_per_step": 1e3 * wall / nsteps})
+                print(json.dumps({"study": "stokes", "row": rows[-1]}), flush=True)
+    print(json.dumps({"study": "stokes", "workload": "two periodic shear layers, nu = 1e-3, to t = 0.25, "
+                                                     "viscous time step from the smallest sub-tet length",
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = _args()
     if args.study == "convergence":
         convergence(args)
+        return
+    if args.study == "stokes":
+        stokes(args)
         return
     if args.serve:
         serve(args)

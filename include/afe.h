@@ -70,6 +70,10 @@ typedef struct {
   double picard_tol;  /* stop when max|q^{r+1}-q^r| <= tol * max(1, max|q^r|), per cell       */
   int picard_max;     /* iteration cap; hitting it is reported as AFE_ENOCONV                  */
   double period[3];   /* domain period per axis; used for sub-tet vertices with image shifts   */
+  int visc_dt_subtet; /* 0: the viscous term of Eq. timestep uses the cell length h_i, as printed;
+                         1: it uses the cell's smallest sub-tet length min_k 6|T_k|/|dT_k|,
+                         a stricter bound under which viscous runs on subgrids with thin
+                         sub-tets stay stable (see the measurements)                          */
 } afe_params;
 
 typedef struct {

@@ -79,3 +79,20 @@ def taylor_green_3d(x, p0=100.0, gamma=GAMMA):
     w = np.zeros_like(u)
     p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
     return primitive_to_conserved(np.ones_like(u), np.stack([u, v, w], 1), p, gamma)
+
+
+def shear_layers(x, nu, t=0.0, v_in=0.1, v_out=-0.1, t0=0.05, gamma=GAMMA):
+    """Periodic form of the first problem of Stokes (Sec. 5, viscous tests): rho = 1,
+    p = 1/gamma, u = w = 0 and the shear velocity v(x) = v_in on 1/4 < x < 3/4, v_out outside,
+    each jump diffused as an error function of width 2 sqrt(nu (t + t0)).  Exact for the
+    linearised (incompressible) shear flow while the two layers do not overlap, i.e. for
+    sqrt(nu (t + t0)) well below 1/4; ``t`` gives the closed form at a later time."""
+    X = np.asarray(x, np.float64)[:, 0] % 1.0
+    s = 2.0 * math.sqrt(nu * (t + t0))
+    from scipy.special import erf
+    # rises from v_out to v_in at x = 1/4, falls back at x = 3/4
+    v = v_out + 0.5 * (v_in - v_out) * (erf((X - 0.25) / s) - erf((X - 0.75) / s))
+    n = len(v)
+    vel = np.zeros((n, 3))
+    vel[:, 1] = v
+    return primitive_to_conserved(np.ones(n), vel, np.full(n, 1.0 / gamma), gamma)

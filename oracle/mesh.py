@@ -30,7 +30,7 @@ from .refelem import ref_element
 
 class CellData:
     __slots__ = ("nodes", "X", "A", "det", "adj", "Jinv", "M", "Minv", "wvec", "vol",
-                 "bfaces", "area", "h", "node_key")
+                 "bfaces", "area", "h", "hsub", "node_key")
 
 
 class BoundaryTri:
@@ -155,6 +155,11 @@ class OracleMesh:
         area = sum(b.area for b in bf)
         cd.area = area
         cd.h = 6.0 * cd.vol / area
+        # smallest sub-tet length 6 |T_k| / |dT_k| (option of the time step's viscous term)
+        faces = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+        cd.hsub = min(cd.det[k] / sum(0.5 * np.linalg.norm(np.cross(X[b] - X[a], X[c] - X[a]))
+                                      for a, b, c in faces)
+                      for k, X in enumerate(cd.X))
         return cd
 
     def _match_faces(self):

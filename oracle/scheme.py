@@ -33,6 +33,7 @@ class Params:
     m1: float = 0.1           # Sec. 4.5
     picard_tol: float = 1e-12
     picard_max: int = 64
+    visc_dt_subtet: bool = False  # viscous term of the time step with the smallest sub-tet length
 
     @property
     def cv(self):
@@ -144,7 +145,8 @@ def cfl_dt(mesh: OracleMesh, u_cells, mu_c, prm: Params):
         rho, v, p = primitives(u, prm.gamma)
         lam = np.linalg.norm(v, axis=1) + sound_speed(rho, p, prm.gamma)
         lv = viscous_eigen(rho, mu_c[i], cell_kappa(mu_c[i], prm), prm)
-        worst = max(worst, float(np.max(lam + 2.0 * lv * (2 * N + 1) / cd.h)))
+        hv = cd.hsub if prm.visc_dt_subtet else cd.h
+        worst = max(worst, float(np.max(lam + 2.0 * lv * (2 * N + 1) / hv)))
     return prm.cfl * mesh.h_min / ((2 * N + 1) * worst)
 
 

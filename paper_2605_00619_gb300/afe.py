@@ -40,6 +40,7 @@ class afe_params(ctypes.Structure):
         ("picard_tol", ctypes.c_double),
         ("picard_max", ctypes.c_int),
         ("period", ctypes.c_double * 3),
+        ("visc_dt_subtet", ctypes.c_int),
     ]
 
 

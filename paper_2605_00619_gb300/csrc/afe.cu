@@ -307,6 +307,7 @@ afe_status check_params(const afe_params* p) {
   if (!(p->gamma > 1.0) || !(p->R > 0.0) || !(p->cfl > 0.0) || !(p->picard_tol > 0.0) || p->picard_max < 1)
     return fail(AFE_EINVAL, "gamma > 1, R > 0, cfl > 0, picard_tol > 0 and picard_max >= 1 are required");
   if (p->mu < 0.0) return fail(AFE_EINVAL, "mu must be >= 0");
+  if (p->visc_dt_subtet != 0 && p->visc_dt_subtet != 1) return fail(AFE_EINVAL, "visc_dt_subtet must be 0 or 1");
   if (p->kappa < 0.0 && !(p->Pr > 0.0)) return fail(AFE_EINVAL, "Pr > 0 is required when kappa < 0");
   return AFE_OK;
 }
@@ -413,6 +414,8 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
   AFE_TRY(M->upload((int64_t**)&d.group_slot, T.group_slot));
   AFE_TRY(M->upload((double**)&d.cell_vol, T.cell_vol));
   AFE_TRY(M->upload((double**)&d.cell_h, T.cell_h));
+  if (p->visc_dt_subtet) AFE_TRY(M->upload((double**)&d.cell_hv, T.cell_hsub));
+  else d.cell_hv = d.cell_h;
   AFE_TRY(M->alloc(&d.wvec, T.n_nodes));
   const int64_t nminv = T.minv_ptr[T.C];
   AFE_TRY(M->alloc(&d.minv64, nminv));

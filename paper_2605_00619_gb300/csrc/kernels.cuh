@@ -51,6 +51,7 @@ struct DevMesh {
   const int64_t* group_slot;
   const double* cell_vol;
   const double* cell_h;
+  const double* cell_hv;  // length in the viscous term of the time step (cell_h or the sub-tet length)
   double* wvec;
   double* minv64;
   float* minv32;
@@ -441,7 +442,7 @@ __global__ void cfl_kernel(const __grid_constant__ Batch bt) {
   const int hh = batch_find(bt.cpre, bt.nh, gc);
   const DevMesh& m = bt.tab[hh];
   const int64_t c = gc - bt.cpre[hh];
-  const double mu_i = m.mu[c], kap = cell_kappa(m, mu_i), h = m.cell_h[c];
+  const double mu_i = m.mu[c], kap = cell_kappa(m, mu_i), h = m.cell_hv[c];
   // per cell: lambda_v = max(4 mu / 3, kappa / c_v) / rho, weighted by 2 (2N+1) / h
   const double gam = m.gamma, visc = fmax(4.0 * mu_i / 3.0, kap / m.cv) * (2.0 * (2 * m.N + 1) / h);
   double best = 0.0;

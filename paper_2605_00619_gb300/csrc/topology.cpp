@@ -63,6 +63,7 @@ struct CellOut {
   std::vector<uint32_t> inc;
   std::vector<SlotTmp> slots;
   double vol = 0;
+  double hsub = 1e300;  // smallest 6 |T_k| / |dT_k| over the cell's sub-tets
 };
 
 inline uint64_t pack_node(int n, const int* lv, const int* al) {
@@ -144,6 +145,19 @@ void process_cell(const RefData& R, const double* xyz, const int64_t* vtx, const
     g[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
     g[9] = det;
     out->vol += det / 6.0;
+    {
+      auto tri = [&](int a, int b, int c) {  // area of the sub-tet face (a, b, c)
+        double u[3], v[3];
+        for (int d = 0; d < 3; ++d) {
+          u[d] = P[b][d] - P[a][d];
+          v[d] = P[c][d] - P[a][d];
+        }
+        const double x = u[1] * v[2] - u[2] * v[1], y = u[2] * v[0] - u[0] * v[2], z = u[0] * v[1] - u[1] * v[0];
+        return 0.5 * std::sqrt(x * x + y * y + z * z);
+      };
+      const double area = tri(0, 1, 2) + tri(0, 1, 3) + tri(0, 2, 3) + tri(1, 2, 3);
+      out->hsub = std::min(out->hsub, det / area);  // 6 (det / 6) / area
+    }
     for (int m = 0; m < 4; ++m) {
       int found = -1;
       for (size_t q = 0; q < lverts.size(); ++q)
@@ -386,6 +400,7 @@ int build_topology(const RefData& R, int64_t n_vertices, const double* xyz, int6
   T.slot_nbr.assign(T.n_slots, -1);
   T.cell_vol.resize(n_cells);
   T.cell_h.resize(n_cells);
+  T.cell_hsub.resize(n_cells);
 
   for (int64_t c = 0; c < n_cells; ++c) {
     const CellOut& co = cells[c];
@@ -394,6 +409,7 @@ int build_topology(const RefData& R, int64_t n_vertices, const double* xyz, int6
     std::copy(co.xyz.begin(), co.xyz.end(), T.node_xyz.begin() + T.node_ptr[c] * 3);
     for (int n = 0; n < co.Ni; ++n) T.inc_ptr[T.node_ptr[c] + n + 1] = co.inc_cnt[n];
     T.cell_vol[c] = co.vol;
+    T.cell_hsub[c] = co.hsub;
     for (size_t s = 0; s < co.slots.size(); ++s) {
       int64_t g = T.slot_ptr[c] + (int64_t)s;
       const SlotTmp& sl = co.slots[s];

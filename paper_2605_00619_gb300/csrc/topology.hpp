@@ -55,6 +55,7 @@ struct Topology {
 
   std::vector<double> cell_vol;    // |P_i|
   std::vector<double> cell_h;      // 6 |P_i| / |dP_i|
+  std::vector<double> cell_hsub;   // min over the cell's sub-tets of 6 |T_k| / |dT_k|
   double h_min = 0;
 };
 

@@ -365,3 +365,27 @@ def test_navier_stokes_step_free_stream_and_conservation(N):
     t1 = scheme.conserved_totals(m, new)
     np.testing.assert_allclose(t1, t0, rtol=0, atol=1e-12 * np.abs(t0).max())
     assert info.iterations.max() < prm.picard_max
+
+
+def test_subtet_length_of_a_cube_cell_and_the_viscous_time_step_option():
+    """The smallest sub-tet length 6|T|/|dT| of the fan subgrid of a unit-lattice cube cell
+    (brute force over the sub-tets here), and the option that puts it into the viscous term
+    of Eq. timestep: equal steps without viscosity, a smaller step with it."""
+    from inputs.voronoi import periodic_voronoi
+    from oracle.mesh import from_polymesh
+    from inputs import states
+    pm = periodic_voronoi(2, lloyd=0)
+    m = from_polymesh(pm, 1)
+    cd = m.cells[0]
+    brute = min(abs(np.linalg.det(X[1:] - X[0])) /
+                sum(0.5 * np.linalg.norm(np.cross(X[b] - X[a], X[c] - X[a]))
+                    for a, b, c in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)))
+                for X in cd.X)
+    assert cd.hsub == pytest.approx(brute, rel=1e-12)
+    assert cd.hsub < cd.h
+    u = m.split(states.constant(m.node_coords()))
+    base = scheme.Params()
+    opt = scheme.Params(visc_dt_subtet=True)
+    assert scheme.cfl_dt(m, u, [0.0] * m.n_cells, base) == scheme.cfl_dt(m, u, [0.0] * m.n_cells, opt)
+    mu = [0.05] * m.n_cells
+    assert scheme.cfl_dt(m, u, mu, opt) < scheme.cfl_dt(m, u, mu, base)

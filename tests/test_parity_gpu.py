@@ -101,6 +101,21 @@ def test_navier_stokes_taylor_green(afe):
     pr.close()
 
 
+def test_navier_stokes_subtet_viscous_time_step(afe):
+    """The option that bounds the viscous time step by the smallest sub-tet length."""
+    pm = periodic_voronoi(2)
+    p = afe.afe_default_params(2, equations=afe.AFE_NAVIER_STOKES, mu=0.05, kappa=-1.0, Pr=0.71, visc_dt_subtet=1)
+    pr = Pair(pm, p)
+    pr.set_state(states.taylor_green_3d(2 * math.pi * pr.om.node_coords(), p0=10.0))
+    for _ in range(2):
+        info = pr.oracle_step()
+        assert pr.lib_step() == 0
+    s = afe.afe_get_stats(pr.h)
+    assert abs(s.dt - info.dt) <= 1e-13 * info.dt
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
 @pytest.mark.parametrize("N", [1, 2, 3])
 def test_fp32_path_within_1e5(afe, N):
     pm = periodic_voronoi(3 if N < 3 else 2)
