@@ -74,6 +74,11 @@ typedef struct {
                          1: it uses the cell's smallest sub-tet length min_k 6|T_k|/|dT_k|,
                          a stricter bound under which viscous runs on subgrids with thin
                          sub-tets stay stable (see the measurements)                          */
+  int h_diameter;     /* 0: h_i = 6|P_i| / |dP_i| (insphere-equivalent diameter; Sec. 4.2 leaves the
+                         length open); 1: h_i = the cell's diameter, the largest distance
+                         between two of its vertices (the example Sec. 4.2 names).  h_i enters
+                         the time step (Eq. timestep), the face penalty of Eq. 3.33 and the
+                         artificial viscosity of Sec. 4.5                                    */
 } afe_params;
 
 typedef struct {

@@ -19,7 +19,8 @@ Follows Sec. 4.1 and the matrix definitions of Sec. 4.3-4.4:
   boundary; it is matched to the sub-triangle of the neighbour cell with the
   same vertices (and periodic image) or marked as a domain-boundary face.
 * h_i = 6|P_i| / |dP_i| (the characteristic length of Sec. 4.2, read as the
-  insphere-equivalent diameter).
+  insphere-equivalent diameter); the cell's diameter (largest vertex distance, the paper's
+  example) is kept beside it for the option that uses it instead.
 """
 from __future__ import annotations
 
@@ -30,7 +31,7 @@ from .refelem import ref_element
 
 class CellData:
     __slots__ = ("nodes", "X", "A", "det", "adj", "Jinv", "M", "Minv", "wvec", "vol",
-                 "bfaces", "area", "h", "hsub", "node_key")
+                 "bfaces", "area", "h", "hsub", "diam", "node_key")
 
 
 class BoundaryTri:
@@ -160,6 +161,9 @@ class OracleMesh:
         cd.hsub = min(cd.det[k] / sum(0.5 * np.linalg.norm(np.cross(X[b] - X[a], X[c] - X[a]))
                                       for a, b, c in faces)
                       for k, X in enumerate(cd.X))
+        # diameter: the largest distance between two vertices of the cell
+        V = cd.X.reshape(-1, 3)
+        cd.diam = float(np.sqrt(((V[:, None, :] - V[None, :, :]) ** 2).sum(-1).max()))
         return cd
 
     def _match_faces(self):

@@ -34,6 +34,7 @@ class Params:
     picard_tol: float = 1e-12
     picard_max: int = 64
     visc_dt_subtet: bool = False  # viscous term of the time step with the smallest sub-tet length
+    h_diameter: bool = False      # h_i = the cell's diameter instead of 6|P_i| / |dP_i|
 
     @property
     def cv(self):
@@ -129,12 +130,18 @@ def limiter(mesh: OracleMesh, u_cells, prm: Params):
         div /= cd.vol
         beta[i] = min(1.0, max(0.0, -(div + prm.m1 * cmin) / (prm.m1 * cmin)))
         lam = np.linalg.norm(v[i]) + c[i]
-        mu_c[i] = prm.mu + beta[i] * rho[i] * lam * cd.h / (2 * mesh.N + 1)
+        mu_c[i] = prm.mu + beta[i] * rho[i] * lam * cell_length(cd, prm) / (2 * mesh.N + 1)
     return beta, mu_c
 
 
 # ---------------------------------------------------------------------------
 # Sec. 4.2 time step
+
+
+def cell_length(cd, prm: Params) -> float:
+    """The characteristic length h_i of Sec. 4.2: 6|P_i| / |dP_i|, or the cell's diameter
+    (the paper's example) when ``prm.h_diameter``."""
+    return cd.diam if prm.h_diameter else cd.h
 
 
 def cfl_dt(mesh: OracleMesh, u_cells, mu_c, prm: Params):
@@ -145,9 +152,10 @@ def cfl_dt(mesh: OracleMesh, u_cells, mu_c, prm: Params):
         rho, v, p = primitives(u, prm.gamma)
         lam = np.linalg.norm(v, axis=1) + sound_speed(rho, p, prm.gamma)
         lv = viscous_eigen(rho, mu_c[i], cell_kappa(mu_c[i], prm), prm)
-        hv = cd.hsub if prm.visc_dt_subtet else cd.h
+        hv = cd.hsub if prm.visc_dt_subtet else cell_length(cd, prm)
         worst = max(worst, float(np.max(lam + 2.0 * lv * (2 * N + 1) / hv)))
-    return prm.cfl * mesh.h_min / ((2 * N + 1) * worst)
+    h_min = min(cell_length(cd, prm) for cd in mesh.cells)
+    return prm.cfl * h_min / ((2 * N + 1) * worst)
 
 
 # ---------------------------------------------------------------------------
@@ -298,9 +306,9 @@ def step(mesh: OracleMesh, u_cells, prm: Params, dt=None, cells=None):
                 qbar_j, Fbar_j = pred[bt.nbr]
                 qp = qbar_j[nb.nodes]
                 Fp = Fbar_j[nb.k][nb.local]
-                hp, mup, kp = mesh.cells[bt.nbr].h, mu_c[bt.nbr], kap[bt.nbr]
+                hp, mup, kp = cell_length(mesh.cells[bt.nbr], prm), mu_c[bt.nbr], kap[bt.nbr]
             else:  # transmissive boundary: outer state = inner state
-                qp, Fp, hp, mup, kp = qm, Fm, cd.h, mu_c[i], kap[i]
+                qp, Fp, hp, mup, kp = qm, Fm, cell_length(cd, prm), mu_c[i], kap[i]
             sides.append((qm, Fm, qp, Fp, hp, mup, kp))
         # wave speeds: max over all nodes of the polyhedral face, both sides (Eq. 3.33)
         smax: dict = {}
@@ -316,7 +324,8 @@ def step(mesh: OracleMesh, u_cells, prm: Params, dt=None, cells=None):
             vmax[bt.group] = max(vmax.get(bt.group, 0.0), sv)
         Gs = []
         for bt, (qm, Fm, qp, Fp, hp, mup, kp) in zip(cd.bfaces, sides):
-            Gs.append(rusanov(qm, Fm, qp, Fp, bt.normal, smax[bt.group], vmax[bt.group], cd.h, hp, N))
+            Gs.append(rusanov(qm, Fm, qp, Fp, bt.normal, smax[bt.group], vmax[bt.group], cell_length(cd, prm),
+                              hp, N))
         face = face_term(mesh, i, Gs)
         new[i] = u_cells[i] + cd.Minv @ (vol - face)
     return new, StepInfo(dt=dt, iterations=iters, beta=beta, mu=mu_c)

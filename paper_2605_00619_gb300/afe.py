@@ -41,6 +41,7 @@ class afe_params(ctypes.Structure):
         ("picard_max", ctypes.c_int),
         ("period", ctypes.c_double * 3),
         ("visc_dt_subtet", ctypes.c_int),
+        ("h_diameter", ctypes.c_int),
     ]
 
 

@@ -308,6 +308,7 @@ afe_status check_params(const afe_params* p) {
     return fail(AFE_EINVAL, "gamma > 1, R > 0, cfl > 0, picard_tol > 0 and picard_max >= 1 are required");
   if (p->mu < 0.0) return fail(AFE_EINVAL, "mu must be >= 0");
   if (p->visc_dt_subtet != 0 && p->visc_dt_subtet != 1) return fail(AFE_EINVAL, "visc_dt_subtet must be 0 or 1");
+  if (p->h_diameter != 0 && p->h_diameter != 1) return fail(AFE_EINVAL, "h_diameter must be 0 or 1");
   if (p->kappa < 0.0 && !(p->Pr > 0.0)) return fail(AFE_EINVAL, "Pr > 0 is required when kappa < 0");
   return AFE_OK;
 }
@@ -388,7 +389,9 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
   d.Pr = p->Pr;
   d.kappa0 = (p->equations == AFE_NAVIER_STOKES) ? p->kappa : (p->kappa < 0 ? 0.0 : p->kappa);
   d.tol = p->picard_tol;
-  d.h_min = T.h_min;
+  // the characteristic length h_i (Sec. 4.2): insphere-equivalent diameter or the diameter
+  const std::vector<double>& hcell = p->h_diameter ? T.cell_diam : T.cell_h;
+  d.h_min = p->h_diameter ? *std::min_element(hcell.begin(), hcell.end()) : T.h_min;
   d.picard_max = p->picard_max;
   d.limiter = p->limiter;
   d.eq = p->equations;
@@ -413,7 +416,7 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
   AFE_TRY(M->upload((int64_t**)&d.group_ptr, T.group_ptr));
   AFE_TRY(M->upload((int64_t**)&d.group_slot, T.group_slot));
   AFE_TRY(M->upload((double**)&d.cell_vol, T.cell_vol));
-  AFE_TRY(M->upload((double**)&d.cell_h, T.cell_h));
+  AFE_TRY(M->upload((double**)&d.cell_h, hcell));
   if (p->visc_dt_subtet) AFE_TRY(M->upload((double**)&d.cell_hv, T.cell_hsub));
   else d.cell_hv = d.cell_h;
   AFE_TRY(M->alloc(&d.wvec, T.n_nodes));

@@ -64,6 +64,7 @@ struct CellOut {
   std::vector<SlotTmp> slots;
   double vol = 0;
   double hsub = 1e300;  // smallest 6 |T_k| / |dT_k| over the cell's sub-tets
+  double diam = 0;      // largest distance between two vertices of the cell
 };
 
 inline uint64_t pack_node(int n, const int* lv, const int* al) {
@@ -89,6 +90,7 @@ void process_cell(const RefData& R, const double* xyz, const int64_t* vtx, const
     return;
   }
   std::vector<VKey> lverts;  // local vertex table
+  std::vector<double> lxyz;  // its coordinates (periodic images applied)
   std::vector<std::array<int, 4>> sub_lv(S);
   std::vector<std::array<double, 12>> X(S);
   out->geo.resize((size_t)S * 10);
@@ -168,6 +170,9 @@ void process_cell(const RefData& R, const double* xyz, const int64_t* vtx, const
       if (found < 0) {
         found = (int)lverts.size();
         lverts.push_back(vk[m]);
+        lxyz.push_back(P[m][0]);
+        lxyz.push_back(P[m][1]);
+        lxyz.push_back(P[m][2]);
       }
       sub_lv[k][m] = found;
       for (int d = 0; d < 3; ++d) X[k][m * 3 + d] = P[m][d];
@@ -178,6 +183,16 @@ void process_cell(const RefData& R, const double* xyz, const int64_t* vtx, const
     out->msg = "cell with too many vertices";
     return;
   }
+  for (size_t a = 0; a < lverts.size(); ++a)
+    for (size_t b = a + 1; b < lverts.size(); ++b) {
+      double d2 = 0;
+      for (int d = 0; d < 3; ++d) {
+        const double e = lxyz[a * 3 + d] - lxyz[b * 3 + d];
+        d2 += e * e;
+      }
+      out->diam = std::max(out->diam, d2);
+    }
+  out->diam = std::sqrt(out->diam);
 
   // AFE nodes: the union without repetition of the sub-tets' P_N nodes (Sec. 4.1)
   std::unordered_map<uint64_t, int> nodes;
@@ -401,6 +416,7 @@ int build_topology(const RefData& R, int64_t n_vertices, const double* xyz, int6
   T.cell_vol.resize(n_cells);
   T.cell_h.resize(n_cells);
   T.cell_hsub.resize(n_cells);
+  T.cell_diam.resize(n_cells);
 
   for (int64_t c = 0; c < n_cells; ++c) {
     const CellOut& co = cells[c];
@@ -410,6 +426,7 @@ int build_topology(const RefData& R, int64_t n_vertices, const double* xyz, int6
     for (int n = 0; n < co.Ni; ++n) T.inc_ptr[T.node_ptr[c] + n + 1] = co.inc_cnt[n];
     T.cell_vol[c] = co.vol;
     T.cell_hsub[c] = co.hsub;
+    T.cell_diam[c] = co.diam;
     for (size_t s = 0; s < co.slots.size(); ++s) {
       int64_t g = T.slot_ptr[c] + (int64_t)s;
       const SlotTmp& sl = co.slots[s];

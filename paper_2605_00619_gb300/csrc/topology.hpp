@@ -56,6 +56,7 @@ struct Topology {
   std::vector<double> cell_vol;    // |P_i|
   std::vector<double> cell_h;      // 6 |P_i| / |dP_i|
   std::vector<double> cell_hsub;   // min over the cell's sub-tets of 6 |T_k| / |dT_k|
+  std::vector<double> cell_diam;   // largest distance between two vertices of the cell
   double h_min = 0;
 };
 

@@ -18,7 +18,7 @@ def oracle_params(p) -> scheme.Params:
     return scheme.Params(gamma=p.gamma, R=p.R, mu=p.mu if ns else 0.0, Pr=p.Pr,
                          kappa=p.kappa if ns else max(p.kappa, 0.0), cfl=p.cfl, limiter=bool(p.limiter),
                          m1=p.m1, picard_tol=p.picard_tol, picard_max=p.picard_max,
-                         visc_dt_subtet=bool(p.visc_dt_subtet))
+                         visc_dt_subtet=bool(p.visc_dt_subtet), h_diameter=bool(p.h_diameter))
 
 
 def node_permutation(om, lib_xyz, lib_ptr):

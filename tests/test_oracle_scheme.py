@@ -367,25 +367,82 @@ def test_navier_stokes_step_free_stream_and_conservation(N):
     assert info.iterations.max() < prm.picard_max
 
 
-def test_subtet_length_of_a_cube_cell_and_the_viscous_time_step_option():
-    """The smallest sub-tet length 6|T|/|dT| of the fan subgrid of a unit-lattice cube cell
-    (brute force over the sub-tets here), and the option that puts it into the viscous term
-    of Eq. timestep: equal steps without viscosity, a smaller step with it."""
-    from inputs.voronoi import periodic_voronoi
-    from oracle.mesh import from_polymesh
-    from inputs import states
-    pm = periodic_voronoi(2, lloyd=0)
-    m = from_polymesh(pm, 1)
+class _CubeMesh:
+    """One cube cell [0, a]^3 with its fan subgrid, built by hand: each face is split into
+    four triangles (two adjacent corners and the face centre), each closed by the cube's
+    centre into a sub-tet; 24 congruent sub-tets, transmissive boundary."""
+
+    def __init__(self, a):
+        corners = [(i, j, k) for i in (0, 1) for j in (0, 1) for k in (0, 1)]
+        xyz = [np.array(c, float) * a for c in corners]
+        centre = len(xyz)
+        xyz.append(np.full(3, 0.5 * a))
+        vtx = []
+        for d in range(3):
+            e1, e2 = (d + 1) % 3, (d + 2) % 3
+            for side in (0, 1):
+                fc = np.full(3, 0.5 * a)
+                fc[d] = side * a
+                f = len(xyz)
+                xyz.append(fc)
+                ring = []
+                for u, v in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                    c = [0, 0, 0]
+                    c[d], c[e1], c[e2] = side, u, v
+                    ring.append(corners.index(tuple(c)))
+                for r in range(4):
+                    vtx.append((centre, f, ring[r], ring[(r + 1) % 4]))
+        self.xyz = np.array(xyz)
+        self.cell_subtet_ptr = np.array([0, len(vtx)])
+        self.subtet_vtx = np.array(vtx)
+        self.subtet_shift = None
+        self.period = np.zeros(3)
+        self.periodic = False
+
+
+def test_cell_lengths_of_a_cube_cell_and_the_options_that_use_them():
+    """The characteristic lengths of a cube cell of side a with its fan subgrid, in closed
+    form: 6|P|/|dP| = a, diameter sqrt(3) a, and every sub-tet (base a^2/4 on a face, apex
+    at the centre, height a/2) has volume a^3/24 and surface a^2 (1/4 + 1/sqrt 2), so
+    6|T|/|dT| = a / (1 + 2 sqrt 2).  On a constant state without viscosity the time step
+    scales with h_min: the diameter option multiplies it by sqrt(3) exactly and the sub-tet
+    option leaves it unchanged; with viscosity the sub-tet option gives a smaller step."""
+    a = 0.37
+    m = from_polymesh(_CubeMesh(a), 1)
     cd = m.cells[0]
-    brute = min(abs(np.linalg.det(X[1:] - X[0])) /
-                sum(0.5 * np.linalg.norm(np.cross(X[b] - X[a], X[c] - X[a]))
-                    for a, b, c in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)))
-                for X in cd.X)
-    assert cd.hsub == pytest.approx(brute, rel=1e-12)
-    assert cd.hsub < cd.h
+    assert len(cd.X) == 24
+    assert cd.vol == pytest.approx(a ** 3, rel=1e-14)
+    assert cd.h == pytest.approx(a, rel=1e-14)
+    assert cd.diam == pytest.approx(math.sqrt(3.0) * a, rel=1e-14)
+    assert cd.hsub == pytest.approx(a / (1.0 + 2.0 * math.sqrt(2.0)), rel=1e-14)
     u = m.split(states.constant(m.node_coords()))
-    base = scheme.Params()
-    opt = scheme.Params(visc_dt_subtet=True)
-    assert scheme.cfl_dt(m, u, [0.0] * m.n_cells, base) == scheme.cfl_dt(m, u, [0.0] * m.n_cells, opt)
+    zero = [0.0] * m.n_cells
+    base = scheme.cfl_dt(m, u, zero, scheme.Params())
+    assert scheme.cfl_dt(m, u, zero, scheme.Params(h_diameter=True)) == pytest.approx(math.sqrt(3.0) * base,
+                                                                                        rel=1e-14)
+    assert scheme.cfl_dt(m, u, zero, scheme.Params(visc_dt_subtet=True)) == base
     mu = [0.05] * m.n_cells
-    assert scheme.cfl_dt(m, u, mu, opt) < scheme.cfl_dt(m, u, mu, base)
+    assert scheme.cfl_dt(m, u, mu, scheme.Params(visc_dt_subtet=True)) < scheme.cfl_dt(m, u, mu, scheme.Params())
+
+
+def test_diameter_option_changes_only_the_cell_length():
+    """With h_i the diameter, a step equals the default step on the same mesh with every
+    6|P|/|dP| overwritten by the cell's diameter (same dt, beta, mu and state): the option
+    reaches the time step, the artificial viscosity and the face penalty, and nothing else."""
+    pm = box_voronoi(2)
+    m1 = from_polymesh(pm, 1)
+    m2 = from_polymesh(pm, 1)
+    for cd in m2.cells:
+        assert cd.diam > cd.h
+        cd.h = cd.diam
+    x = m1.node_coords()
+    c = x.mean(axis=0)
+    u0 = states.primitive_to_conserved(1.0 + 0.1 * np.sin(x.sum(axis=1)), -(x - c), 1.0)  # compression
+    prm = dict(limiter=True, mu=0.01, kappa=-1.0)
+    a, ia = scheme.step(m1, m1.split(u0), scheme.Params(h_diameter=True, **prm))
+    b, ib = scheme.step(m2, m2.split(u0), scheme.Params(**prm))
+    assert ia.dt == ib.dt and ia.dt > 0
+    assert np.max(ia.beta) > 0
+    np.testing.assert_array_equal(ia.mu, ib.mu)
+    for ua, ub in zip(a, b):
+        np.testing.assert_array_equal(ua, ub)

@@ -92,6 +92,28 @@ def test_transmissive_box_with_limiter(afe):
     pr.close()
 
 
+def test_cell_diameter_option_with_limiter_and_viscosity(afe):
+    """h_i = the cell's diameter: it reaches the time step, the artificial viscosity and the
+    face penalty; compressive data on a box mesh so that the limiter is active."""
+    pm = box_voronoi(3)
+    p = afe.afe_default_params(2, limiter=1, equations=afe.AFE_NAVIER_STOKES, mu=0.01, kappa=-1.0, Pr=0.71,
+                               h_diameter=1)
+    pr = Pair(pm, p)
+    x = pr.om.node_coords()
+    pr.set_state(states.primitive_to_conserved(1.0 + 0.1 * np.sin(x.sum(axis=1)), -(x - x.mean(axis=0)), 1.0))
+    for _ in range(2):
+        info = pr.oracle_step()
+        assert pr.lib_step(check=False) in (0, 5)
+        s = afe.afe_get_stats(pr.h)
+        assert abs(s.dt - info.dt) <= 1e-13 * info.dt
+    _, _, beta, mu = afe.afe_get_diagnostics(pr.h, pm.n_cells, qbar=False)
+    assert np.max(info.beta) > 0
+    np.testing.assert_allclose(beta, info.beta, atol=1e-12)
+    np.testing.assert_allclose(mu, info.mu, rtol=1e-12)
+    assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    pr.close()
+
+
 def test_navier_stokes_taylor_green(afe):
     pm = periodic_voronoi(2)
     p = afe.afe_default_params(2, equations=afe.AFE_NAVIER_STOKES, mu=0.005, kappa=-1.0, Pr=0.71)
