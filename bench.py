@@ -63,7 +63,7 @@ def _args():
                     help="shock/tgv: length in the viscous term of the time step (the smallest "
                          "sub-tet length, or the cell length as printed; see the stokes study)")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
-    ap.add_argument("--study", choices=["convergence", "stokes"], help="accuracy study instead of the throughput run")
+    ap.add_argument("--study", choices=["convergence", "stokes", "vortex"], help="accuracy study instead of the throughput run")
     ap.add_argument("--workload", default="density", choices=["density", "shock", "tgv"],
                     help="density: density wave, periodic unit cube, Euler; shock: spherical explosion on "
                          "[-1,1]^3, transmissive, limiter on; tgv: Navier-Stokes Taylor-Green vortex on "
@@ -626,6 +626,65 @@ def convergence(args):
                       "rows": rows, "observed_order": orders}), flush=True)
 
 
+def vortex(args):
+    """Space and space-time accuracy on the isentropic vortex (Sec. 5.1): its steady form and
+    its travelling form (background velocity (1, 1, 0)) on the periodic box [0, 10)^3, to
+    t = 1 with equal steps at the stable CFL, FP32 form, N = 1, 2, 3 on jittered-Voronoi
+    meshes of 8^3, 16^3 and 32^3 cells.  Reported per run (one JSON line each, then a
+    summary line with the observed orders between consecutive meshes): the L1 and L2 errors
+    in rho against the exact solution (the initial state, shifted by (1, 1, 0) t for the
+    travelling form), volume-weighted nodal norms as in the convergence study.
+    """
+    import numpy as np
+    import torch
+
+    from inputs import states
+    from inputs.voronoi import periodic_voronoi
+    from paper_2605_00619_gb300 import afe
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    afe.lib()
+    t_end, L = 1.0, 10.0
+    rows = []
+    for n in (8, 16, 32):
+        pm = periodic_voronoi(n, L=L)
+        sub = pm.subtet_coords()
+        vol_t = np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0
+        cell_of = np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr))
+        vol = np.bincount(cell_of, weights=vol_t, minlength=pm.n_cells)
+        for flow, vel in (("steady", (0.0, 0.0, 0.0)), ("travelling", (1.0, 1.0, 0.0))):
+            for N in (1, 2, 3):
+                p = afe.afe_default_params(N, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128,
+                                           cfl=STABLE_CFL[N])
+                h = afe.create_from_polymesh(pm, p)
+                x = afe.afe_get_node_coords(h)
+                ptr = afe.afe_node_ptr(h, pm.n_cells)
+                afe.afe_set_state(h, states.isentropic_vortex(x, vel=vel, period=L))
+                nsteps = int(math.ceil(t_end / afe.afe_compute_dt(h) - 1e-9))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                afe.afe_step_async(h, t_end / nsteps, nsteps)
+                st = afe.afe_sync(h, check=False)
+                wall = time.perf_counter() - t0
+                q = afe.afe_get_state(h)
+                afe.afe_mesh_destroy(h)
+                e = np.abs(q[:, 0] - states.isentropic_vortex(x, t=t_end, vel=vel, period=L)[:, 0])
+                cnt = np.diff(ptr)
+                l1 = float(np.sum(vol * np.add.reduceat(e, ptr[:-1]) / cnt))
+                l2 = float(np.sqrt(np.sum(vol * np.add.reduceat(e * e, ptr[:-1]) / cnt)))
+                rows.append({"flow": flow, "n": n, "N": N, "steps": nsteps, "l1_rho": l1, "l2_rho": l2,
+                             "status": int(st), "ms_per_step": 1e3 * wall / nsteps})
+                print(json.dumps({"study": "vortex", "row": rows[-1]}), flush=True)
+    orders = {}
+    for flow in ("steady", "travelling"):
+        for N in (1, 2, 3):
+            rs = [r for r in rows if r["flow"] == flow and r["N"] == N]
+            orders[f"{flow}_N{N}"] = [math.log(r0["l2_rho"] / r1["l2_rho"]) / math.log(r1["n"] / r0["n"])
+                                      for r0, r1 in zip(rs, rs[1:])]
+    print(json.dumps({"study": "vortex", "workload": "isentropic vortex, eps 5, periodic [0,10)^3, to t = 1, FP32",
+                      "rows": rows, "observed_order_l2": orders}), flush=True)
+
+
 def stokes(args):
     """Viscous check: periodic form of the first problem of Stokes (two shear layers, nu = mu =
     1e-3 with rho = 1, p = 1/gamma, Navier-Stokes, kappa from Pr 0.71), integrated to t = 0.25
@@ -695,6 +754,9 @@ def main():
         return
     if args.study == "stokes":
         stokes(args)
+        return
+    if args.study == "vortex":
+        vortex(args)
         return
     if args.serve:
         serve(args)

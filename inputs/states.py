@@ -96,3 +96,28 @@ def shear_layers(x, nu, t=0.0, v_in=0.1, v_out=-0.1, t0=0.05, gamma=GAMMA):
     vel = np.zeros((n, 3))
     vel[:, 1] = v
     return primitive_to_conserved(np.ones(n), vel, np.full(n, 1.0 / gamma), gamma)
+
+
+def isentropic_vortex(x, t=0.0, eps=5.0, centre=(5.0, 5.0), vel=(0.0, 0.0, 0.0), period=10.0, gamma=GAMMA):
+    """Two-dimensional isentropic vortex (Sec. 5.1, steady and travelling forms) on the
+    periodic box [0, period)^3: background rho = p = 1 and velocity ``vel``; around the axis
+    through ``centre`` + vel t (parallel to z; the periodic image nearest to each point)
+    the temperature drops by dT = -(gamma-1) eps^2 / (8 gamma pi^2) exp(1 - r^2), with
+    rho = (1 + dT)^(1/(gamma-1)), p = (1 + dT)^(gamma/(gamma-1)), and the swirl
+    (du, dv) = eps / (2 pi) exp((1 - r^2) / 2) (-(y - y_c), x - x_c).  The swirl exponent is
+    read as (1 - r^2)/2 (the printed (1 - gamma^2)/2 does not depend on r).  The state is an
+    exact steady solution of the Euler equations in the vortex's frame; the periodic
+    images it ignores differ from it by O(exp(-(period/2)^2 / 2)) at the box faces."""
+    X = np.asarray(x, np.float64)
+    c = np.asarray(centre, np.float64) + t * np.asarray(vel[:2], np.float64)
+    d = X[:, :2] - c
+    d -= period * np.round(d / period)
+    r2 = np.sum(d * d, axis=1)
+    dT = -(gamma - 1.0) * eps ** 2 / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - r2)
+    rho = (1.0 + dT) ** (1.0 / (gamma - 1.0))
+    p = (1.0 + dT) ** (gamma / (gamma - 1.0))
+    s = eps / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    v = np.tile(np.asarray(vel, np.float64), (len(X), 1))
+    v[:, 0] -= s * d[:, 1]
+    v[:, 1] += s * d[:, 0]
+    return primitive_to_conserved(rho, v, p, gamma)

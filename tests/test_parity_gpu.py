@@ -94,10 +94,12 @@ def test_transmissive_box_with_limiter(afe):
 
 def test_cell_diameter_option_with_limiter_and_viscosity(afe):
     """h_i = the cell's diameter: it reaches the time step, the artificial viscosity and the
-    face penalty; compressive data on a box mesh so that the limiter is active."""
+    face penalty; compressive data on a box mesh so that the limiter is active (with the
+    sub-tet length in the viscous term of the time step, without which this data goes
+    non-finite in the first step)."""
     pm = box_voronoi(3)
     p = afe.afe_default_params(2, limiter=1, equations=afe.AFE_NAVIER_STOKES, mu=0.01, kappa=-1.0, Pr=0.71,
-                               h_diameter=1)
+                               h_diameter=1, visc_dt_subtet=1)
     pr = Pair(pm, p)
     x = pr.om.node_coords()
     pr.set_state(states.primitive_to_conserved(1.0 + 0.1 * np.sin(x.sum(axis=1)), -(x - x.mean(axis=0)), 1.0))
