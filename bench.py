@@ -2,7 +2,9 @@
 
 Workload (one GPU): the smooth density wave rho = 1 + 0.2 sin(2 pi (x+y+z)), u = (1,1,1),
 p = 1 on the periodic unit cube, jittered-lattice Voronoi mesh with 32^3 cells and fan
-subgrids, AFE degree N = 3, CFL 0.3, Euler.  A DOF-update is one conserved variable at one
+subgrids, AFE degree N = 3, Euler, at the largest CFL at which these meshes run the workload
+stably (0.15 at N = 3; the paper's 0.3 diverges on them at N >= 2 and is timed beside it as
+``fp32_paper_cfl``).  A DOF-update is one conserved variable at one
 AFE node advanced by one full ADER step (limiter check, time step, predictor, face fluxes,
 corrector).  ``value`` is the reduced-precision form (FP32 arithmetic, FP64 master state,
 FP64 time step and conservative cell totals); the plain FP64 form is timed beside it.
@@ -34,9 +36,10 @@ METRIC = "DOF-updates/s per ADER-DG step"
 
 # Largest CFL numbers at which the fan-subgrid Voronoi meshes of inputs.voronoi run the
 # density wave stably to t = 0.1 (measured on 16^3 and 32^3 meshes, both forms): the
-# paper's 0.3 holds for N = 1; at N = 2 a 32^3 mesh diverges after ~200 steps at 0.3 and at
-# N = 3 after ~20 steps at 0.3 and ~30 at 0.2.
+# paper's 0.3 holds for N = 1; at N = 2 a 32^3 mesh diverges after ~200 steps at 0.3, and at
+# N = 3 within 8 steps at 0.3 and after ~30 at 0.2.
 STABLE_CFL = {1: 0.3, 2: 0.2, 3: 0.15}
+PAPER_CFL = 0.3
 
 # DRAM bytes (read + write) of one predictor_f32_kernel<3> launch per cell, from the ncu
 # capture summarised in profiles/step_kernels_density_wave_12c_N3.md (907 MB over 1728 cells
@@ -58,7 +61,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cfl", type=float, default=None,
-                    help="CFL number (default: 0.3, the paper's, for the density wave; the stable one otherwise)")
+                    help="CFL number (default: the largest stable one of STABLE_CFL; the paper's is 0.3)")
     ap.add_argument("--visc-dt", default="subtet", choices=["subtet", "cell"],
                     help="shock/tgv: length in the viscous term of the time step (the smallest "
                          "sub-tet length, or the cell length as printed; see the stokes study)")
@@ -97,7 +100,7 @@ from oracle.mesh import from_polymesh
 from oracle import scheme
 pm = periodic_voronoi({n})
 m = from_polymesh(pm, {N})
-prm = scheme.Params(cfl=0.3)
+prm = scheme.Params(cfl={cfl})
 uc = m.split(states.density_wave(m.node_coords()))
 dt = scheme.cfl_dt(m, uc, [0.0] * m.n_cells, prm) * {dt_scale}
 out = []
@@ -109,21 +112,21 @@ print(json.dumps(dict(times=out, dofs=5 * m.n_nodes, cells=m.n_cells, iters=floa
 """
 
 
-def run_oracle(n_sample, N, steps, dt_scale):
+def run_oracle(n_sample, N, steps, dt_scale, cfl):
     """Run the oracle in a fresh single-threaded process; returns its JSON record."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SNIPPET.format(root=ROOT, n=n_sample, N=N, steps=steps, dt_scale=dt_scale)
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=n_sample, N=N, steps=steps, dt_scale=dt_scale, cfl=float(cfl))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample(N, steps):
+def oracle_sample(N, steps, cfl):
     """A bounded sample of the workload for the oracle: full steps of the same generator,
     order and CFL on the 6^3 periodic mesh."""
     n_s = 6
-    return n_s, run_oracle(n_s, N, steps, dt_scale=1.0)
+    return n_s, run_oracle(n_s, N, steps, 1.0, cfl)
 
 
 def reference_arm(args):
@@ -131,12 +134,13 @@ def reference_arm(args):
     if rank != 0:
         return
     n_s = 6
-    rec = run_oracle(n_s, args.order, args.warmup + args.steps, 1.0)
+    cfl = args.cfl if args.cfl is not None else STABLE_CFL[args.order]
+    rec = run_oracle(n_s, args.order, args.warmup + args.steps, 1.0, cfl)
     times = rec["times"][args.warmup:]
     t = sum(times)
     value = rec["dofs"] * len(times) / t
     sample = (f"oracle (numpy FP64, 1 thread) full steps on the {n_s}^3 periodic mesh of the same generator, "
-              f"N={args.order}, CFL 0.3 ({rec['cells']} cells, {rec['dofs']} DOFs per step)")
+              f"N={args.order}, CFL {cfl:g} ({rec['cells']} cells, {rec['dofs']} DOFs per step)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
@@ -375,12 +379,11 @@ def ours(args):
         afe.afe_mesh_destroy(h)
         return rec
 
-    cfl = args.cfl if args.cfl is not None else (0.3 if args.workload == "density" else STABLE_CFL[args.order])
+    cfl = args.cfl if args.cfl is not None else STABLE_CFL[args.order]
     r32 = run_form(afe.AFE_FP32, args.steps, args.warmup, not args.no_e2e, cfl)
     r64 = run_form(afe.AFE_FP64, args.fp64_steps, 1, False, cfl) if args.fp64_steps > 0 else None
-    # the same FP32 step at the largest CFL that stays stable over long runs on these meshes
-    rst = (run_form(afe.AFE_FP32, args.steps, args.warmup, False, STABLE_CFL[args.order])
-           if STABLE_CFL[args.order] != cfl else None)
+    # the same FP32 step at the paper's CFL, which these meshes do not sustain at N >= 2
+    rst = run_form(afe.AFE_FP32, args.steps, args.warmup, False, PAPER_CFL) if cfl != PAPER_CFL else None
 
     K = args.steps
     dofs = 5 * r32["n_nodes"]
@@ -433,10 +436,10 @@ def ours(args):
     out["config"]["cfl"] = cfl
     if rst is not None:
         v_st, ms_st = throughput(red, 5 * rst["n_nodes"], K, rst["ms"])
-        out["fp32_stable_cfl"] = {"cfl": STABLE_CFL[args.order], "value": v_st, "unit": UNIT, "ms_per_step": ms_st / K,
-                                  "picard_iters_mean": rst["iters_mean"], "status": rst["status"],
-                                  "note": "CFL at which these meshes run stably to t = 0.1 (the paper's 0.3 "
-                                          "diverges after some tens of steps at this order)"}
+        out["fp32_paper_cfl"] = {"cfl": PAPER_CFL, "value": v_st, "unit": UNIT, "ms_per_step": ms_st / K,
+                                 "picard_iters_mean": rst["iters_mean"], "status": rst["status"],
+                                 "note": "the paper's CFL; on these meshes it diverges at N >= 2 (status 6: "
+                                         "non-finite), so this timing is not a valid throughput there"}
     if r64 is not None:
         ms64 = max_over_ranks(r64["ms"])
         out["fp64_plain"] = {"value": sum_over_ranks(5 * r64["n_nodes"] * args.fp64_steps) / (ms64 / 1e3),
@@ -447,11 +450,11 @@ def ours(args):
         out["fp32_over_fp64"] = value / out["fp64_plain"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            n_s, rec = oracle_sample(args.order, 1)
+            n_s, rec = oracle_sample(args.order, 1, cfl)
             cb = rec["dofs"] / rec["times"][0]
             out["cpu_baseline"] = {"value": cb, "unit": UNIT, "cores": 1, "kind": "oracle",
                                    "sample": f"one oracle step (numpy FP64, 1 thread) on the {n_s}^3 periodic mesh of "
-                                             f"the same generator, N={args.order} ({rec['cells']} cells, "
+                                             f"the same generator, N={args.order}, CFL {cfl:g} ({rec['cells']} cells, "
                                              f"{rec['dofs']} DOFs, {rec['iters']:.1f} mean fixed-point "
                                              f"iterations)"}
         except Exception as e:  # the baseline never hides the GPU number

@@ -54,7 +54,7 @@ JITTER = 0.3
 COLLAPSE = 0.25
 # fan triangles whose face centre is closer than THIN * (lattice spacing) to their edge
 # mark a thin face; its shortest edge is collapsed too
-THIN = 0.04
+THIN = 0.08
 # Lloyd steps applied to the jittered seeds (each moves a seed to its cell's centroid)
 LLOYD = 4
 
