@@ -104,11 +104,13 @@ prm = scheme.Params(cfl={cfl})
 uc = m.split(states.density_wave(m.node_coords()))
 dt = scheme.cfl_dt(m, uc, [0.0] * m.n_cells, prm) * {dt_scale}
 out = []
+wall0 = time.time()
 for s in range({steps}):
     t0 = time.perf_counter()
     uc, info = scheme.step(m, uc, prm, dt=dt)
     out.append(time.perf_counter() - t0)
-print(json.dumps(dict(times=out, dofs=5 * m.n_nodes, cells=m.n_cells, iters=float(info.iterations.mean()))))
+print(json.dumps(dict(times=out, dofs=5 * m.n_nodes, cells=m.n_cells, iters=float(info.iterations.mean()),
+                      wall=[wall0, time.time()])))
 """
 
 
@@ -120,6 +122,28 @@ def run_oracle(n_sample, N, steps, dt_scale, cfl):
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_all_cores(N, cfl, procs=None):
+    """The same one-step oracle sample run by ``procs`` single-threaded processes at once
+    (default: every host core), each on its own copy of the 6^3 mesh: the host's aggregate
+    oracle throughput over independent problems, all DOF-updates over the span from the
+    first step's start to the last step's end.  Returns (DOF-updates/s, processes)."""
+    procs = procs or os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=6, N=N, steps=1, dt_scale=1.0, cfl=float(cfl))
+    runs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                             env=env) for _ in range(procs)]
+    dofs, starts, ends = 0, [], []
+    for r in runs:
+        out, err = r.communicate()
+        if r.returncode != 0:
+            raise RuntimeError("oracle run failed: " + err[-2000:])
+        rec = json.loads(out.strip().splitlines()[-1])
+        dofs += rec["dofs"]
+        starts.append(rec["wall"][0])
+        ends.append(rec["wall"][1])
+    return dofs / (max(ends) - min(starts)), procs
 
 
 def oracle_sample(N, steps, cfl):
@@ -459,6 +483,14 @@ def ours(args):
                                              f"iterations)"}
         except Exception as e:  # the baseline never hides the GPU number
             out["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": str(e)[:200]}
+        try:
+            v_all, procs = oracle_all_cores(args.order, cfl)
+            out["cpu_baseline_all_cores"] = {
+                "value": v_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+                "sample": f"{procs} single-threaded oracle processes at once, each one step on its own 6^3 mesh, "
+                          f"N={args.order}, CFL {cfl:g} (span from the first step's start to the last step's end)"}
+        except Exception as e:
+            out["cpu_baseline_all_cores"] = {"value": None, "unit": UNIT, "kind": "oracle", "sample": str(e)[:200]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
