@@ -367,6 +367,84 @@ def test_navier_stokes_step_free_stream_and_conservation(N):
     assert info.iterations.max() < prm.picard_max
 
 
+class _LatticeMesh:
+    """n^3 cube cells of side d filling [0, n d]^3 (transmissive box), each split as
+    _CubeMesh splits one; corners and face centres are shared between the cells that
+    touch them, so the subgrid is conforming across cells."""
+
+    def __init__(self, n, d):
+        ids: dict = {}
+        xyz = []
+
+        def vid(key, pos):
+            if key not in ids:
+                ids[key] = len(xyz)
+                xyz.append(np.asarray(pos, float) * d)
+            return ids[key]
+
+        vtx, ptr = [], [0]
+        for ci in range(n):
+            for cj in range(n):
+                for ck in range(n):
+                    base = np.array([ci, cj, ck], float)
+                    centre = vid(("c", ci, cj, ck), base + 0.5)
+                    for ax in range(3):
+                        e1, e2 = (ax + 1) % 3, (ax + 2) % 3
+                        for side in (0, 1):
+                            fpos = base + 0.5
+                            fpos[ax] = base[ax] + side
+                            f = vid(("f", ax) + tuple(int(2 * t) for t in fpos), fpos)
+                            ring = []
+                            for u, v in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                                c = [0, 0, 0]
+                                c[ax], c[e1], c[e2] = side, u, v
+                                g = tuple(int(b) + int(o) for b, o in zip(base, c))
+                                ring.append(vid(("v",) + g, g))
+                            for r in range(4):
+                                vtx.append((centre, f, ring[r], ring[(r + 1) % 4]))
+                    ptr.append(len(vtx))
+        self.xyz = np.array(xyz)
+        self.cell_subtet_ptr = np.array(ptr)
+        self.subtet_vtx = np.array(vtx)
+        self.subtet_shift = None
+        self.period = np.zeros(3)
+        self.periodic = False
+
+
+def test_limiter_detector_closed_form_on_a_cube_lattice():
+    """The detector of Sec. 4.5 on a regular lattice of cubes (side d) with a uniform
+    compression v = a (x - x0), rho and p uniform: cell means of a linear field are its
+    values at the cell centres, neighbouring centres are d apart along the face normals, so
+    for an interior cell the face sum (1/|P|) sum_f |f| (v_nbr - v_i) . n equals 6 a
+    (the formula as printed, without a factor 1/2).  The sound speed comes from the cell
+    means of the conserved variables: rho E = p/(gamma-1) + |v|^2/2 is quadratic, its P1
+    interpolant on a fan sub-tet (values 0, d^2/4, 3d^2/4, 3d^2/4 of |x - c|^2 at the centre,
+    face centre and corners) has mean |v_i|^2 + 7 a^2 d^2 / 16, so the mean pressure is
+    1 + (gamma-1) 7 a^2 d^2 / 32.  Then beta = -(6a + m1 c)/(m1 c) (about 0.5 here) and
+    mu_i = beta (|v_i| + c) h / (2N + 1) with h = d."""
+    n, d = 3, 0.4
+    m = from_polymesh(_LatticeMesh(n, d), 1)
+    prm = scheme.Params(limiter=True)
+    cs = math.sqrt(prm.gamma)
+    a = -1.5 * prm.m1 * cs / 6.0
+    x = m.node_coords()
+    x0 = np.array([0.3, 0.5, 0.7])
+    u = states.primitive_to_conserved(np.ones(len(x)), a * (x - x0), np.ones(len(x)))
+    beta, mu = scheme.limiter(m, m.split(u), prm)
+    centre = [np.mean(c.nodes, axis=0) for c in m.cells]
+    inner = [i for i, c in enumerate(m.cells) if all(bt.nbr >= 0 for bt in c.bfaces)]
+    assert len(inner) == (n - 2) ** 3
+    pbar = 1.0 + (prm.gamma - 1.0) * 7.0 * a * a * d * d / 32.0
+    cbar = math.sqrt(prm.gamma * pbar)
+    b_ex = -(6.0 * a + prm.m1 * cbar) / (prm.m1 * cbar)
+    assert 0.4 < b_ex < 0.6
+    for i in inner:
+        assert beta[i] == pytest.approx(b_ex, rel=1e-12)
+        lam = np.linalg.norm(a * (centre[i] - x0)) + cbar
+        assert mu[i] == pytest.approx(b_ex * lam * d / 3.0, rel=1e-12)
+    assert np.all((beta >= 0) & (beta <= 1))
+
+
 class _CubeMesh:
     """One cube cell [0, a]^3 with its fan subgrid, built by hand: each face is split into
     four triangles (two adjacent corners and the face centre), each closed by the cube's
