@@ -66,7 +66,7 @@ def _args():
                     help="shock/tgv: length in the viscous term of the time step (the smallest "
                          "sub-tet length, or the cell length as printed; see the stokes study)")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
-    ap.add_argument("--study", choices=["convergence", "stokes", "vortex"], help="accuracy study instead of the throughput run")
+    ap.add_argument("--study", choices=["convergence", "stokes", "vortex", "shock"], help="accuracy study instead of the throughput run")
     ap.add_argument("--workload", default="density", choices=["density", "shock", "tgv"],
                     help="density: density wave, periodic unit cube, Euler; shock: spherical explosion on "
                          "[-1,1]^3, transmissive, limiter on; tgv: Navier-Stokes Taylor-Green vortex on "
@@ -720,6 +720,103 @@ def vortex(args):
                       "rows": rows, "observed_order_l2": orders}), flush=True)
 
 
+def shock_study(args):
+    """The spherical explosion (Sec. 5.4) against its one-dimensional radial reference.
+
+    The ``--workload shock`` problem (box [-1,1]^3, transmissive, limiter on, erf-smoothed
+    over 1.5 lattice spacings, viscous time step from the sub-tet length unless
+    ``--visc-dt cell``) on the ``--n``^3 mesh at order ``--order``, FP32 form, integrated with
+    CFL steps to t = 0.25 (the last step shortened).  The reference is the radial MUSCL
+    solution of ``inputs.radial`` from the same smoothed data on 15,000 cells of
+    r in [0, 1.75].  Reported: volume-weighted nodal L1 errors of rho, |u| and p over the
+    nodes with r < 0.95 (the transmissive faces of the box are at distance 1), and the
+    radius where the shell-averaged density falls across the shock, against the reference's.
+    """
+    import numpy as np
+    import torch
+
+    from inputs import radial, states
+    from inputs.voronoi import box_voronoi
+    from paper_2605_00619_gb300 import afe
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    afe.lib()
+    t_end, N, n = 0.25, args.order, args.n
+    alpha0 = 1.5 * 2.0 / n
+    pm = box_voronoi(n)
+    sub = pm.subtet_coords()
+    vol_t = np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0
+    cell_of = np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr))
+    vol = np.bincount(cell_of, weights=vol_t, minlength=pm.n_cells)
+    p = afe.afe_default_params(N, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128, cfl=STABLE_CFL[N],
+                               limiter=1, visc_dt_subtet=int(args.visc_dt == "subtet"))
+    h = afe.create_from_polymesh(pm, p)
+    x = afe.afe_get_node_coords(h)
+    ptr = afe.afe_node_ptr(h, pm.n_cells)
+    afe.afe_set_state(h, states.spherical_riemann(x, alpha0=alpha0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, steps = 0, 0
+    while True:
+        s = afe.afe_get_stats(h)
+        rem = t_end - s.t
+        if rem <= 1e-12 * t_end:
+            break
+        if steps == 0 or rem > 25.0 * s.dt:
+            k, dt = 20, 0.0
+        elif rem > s.dt:
+            k, dt = 1, 0.0
+        else:
+            k, dt = 1, rem
+        afe.afe_step_async(h, dt, k)
+        st = afe.afe_sync(h, check=False)
+        steps += k
+        if st not in (0, afe.AFE_ENOCONV):
+            status = st
+            break
+        status = status or st
+    wall = time.perf_counter() - t0
+    q = afe.afe_get_state(h)
+    t_reached = afe.afe_get_stats(h).t
+    afe.afe_mesh_destroy(h)
+    rref, wref = radial.explosion_reference(t_end=t_end, n=15000, R=1.75, alpha0=alpha0)
+    cmp = compare_with_radial(x, q, ptr, vol, rref, wref)
+    print(json.dumps({"study": "shock", "workload": workload_name(n, N, "shock") + ", to t = 0.25, FP32",
+                      "status": int(status), "t": t_reached, "steps": steps, "ms_per_step": 1e3 * wall / max(steps, 1),
+                      **cmp, "reference": "radial MUSCL, Rusanov flux, 15000 cells on r in [0, 1.75]"}), flush=True)
+
+
+def compare_with_radial(x, q, ptr, vol, rref, wref, r_max=0.95, ambient=0.125, gamma=1.4):
+    """Nodal state q [n_nodes, 5] at positions x against a radial profile (rref, wref = rho, u,
+    p): volume-weighted nodal L1 errors of rho, |u| and p over the nodes with r < r_max (each
+    cell's volume shared equally by its nodes ptr), and the shock radius of both: the
+    outermost radius below r_max where the (shell-averaged) density exceeds the ambient value
+    by half the reference's jump across its outermost front."""
+    import numpy as np
+
+    r = np.linalg.norm(x, axis=1)
+    rho = q[:, 0]
+    speed = np.linalg.norm(q[:, 1:4], axis=1) / rho
+    pres = (gamma - 1.0) * (q[:, 4] - 0.5 * rho * speed ** 2)
+    ref = [np.interp(r, rref, wref[:, j]) for j in range(3)]
+    cnt = np.diff(ptr)
+    w_node = np.repeat(np.asarray(vol) / cnt, cnt) * (r < r_max)
+    err = {name: float(np.sum(w_node * np.abs(v - rv)) / np.sum(w_node))
+           for name, v, rv in (("rho", rho, ref[0]), ("speed", speed, np.abs(ref[1])), ("p", pres, ref[2]))}
+    bins = np.linspace(0.0, r_max, 96)
+    idx = np.digitize(r, bins) - 1
+    shell = np.array([rho[idx == b].mean() if np.any(idx == b) else np.nan for b in range(len(bins) - 1)])
+    mid = 0.5 * (bins[1:] + bins[:-1])
+    inside = rref < r_max
+    front = rref[np.nonzero(inside & (np.abs(wref[:, 0] - ambient) > 1e-3 * ambient))[0].max()]
+    behind = inside & (rref > front - 0.05)
+    jump = ambient + 0.5 * (wref[behind, 0].max() - ambient)
+    hit = np.nonzero(shell > jump)[0]
+    r_sh = float(mid[hit.max()]) if len(hit) else None
+    r_sh_ref = float(rref[np.nonzero((wref[:, 0] > jump) & inside)[0].max()])
+    return {"l1_vs_radial_reference": err, "shock_radius": r_sh, "shock_radius_reference": r_sh_ref}
+
+
 def stokes(args):
     """Viscous check: periodic form of the first problem of Stokes (two shear layers, nu = mu =
     1e-3 with rho = 1, p = 1/gamma, Navier-Stokes, kappa from Pr 0.71), integrated to t = 0.25
@@ -792,6 +889,9 @@ def main():
         return
     if args.study == "vortex":
         vortex(args)
+        return
+    if args.study == "shock":
+        shock_study(args)
         return
     if args.serve:
         serve(args)
