@@ -554,3 +554,62 @@ def test_viscous_shear_wave_decays_at_the_analytic_rate():
         t += dt
     rate = -math.log(amplitude(uc) / a0) / T
     assert rate == pytest.approx(nu * k * k, rel=0.03)
+
+
+def _run_to(m, uc, prm, mu, T):
+    t = 0.0
+    while t < T - 1e-12:
+        dt = min(scheme.cfl_dt(m, uc, [mu] * m.n_cells, prm), T - t)
+        uc, _ = scheme.step(m, uc, prm, dt=dt)
+        t += dt
+    return uc
+
+
+def _mode(m, values, k):
+    """Least-squares amplitude of sin(k x) in nodal values (cell volume shared by its nodes)."""
+    x = m.node_coords()
+    w = np.concatenate([np.full(len(c.nodes), c.vol / len(c.nodes)) for c in m.cells])
+    s = np.sin(k * x[:, 0])
+    return np.sum(w * s * values) / np.sum(w * s * s)
+
+
+def test_heat_conduction_and_longitudinal_viscosity_closed_forms():
+    """Linearised about rest (rho = 1, R = 1, c = 1), two modes with closed forms:
+    * temperature T' = eps sin(k x) at uniform pressure, kappa > 0, mu = 0: at times short
+      against the acoustic time 1/(c k) the density cannot respond and T' decays at the
+      isochoric rate kappa k^2 / (rho c_v) (the acoustic correction enters at O(t^3));
+    * longitudinal velocity u = A sin(k x), mu > 0, kappa = 0: u'' + b u' + (c k)^2 u = 0 with
+      b = (4/3) mu k^2 / rho and u'(0) = -b A, so u(t) = A exp(-b t / 2) (cos w t -
+      b / (2 w) sin w t), w^2 = (c k)^2 - b^2 / 4.  A factor 1 instead of 4/3 in the normal
+      stress would move the amplitude at t = 0.05 by 0.028; the tolerance is 0.003."""
+    pm, m = mesh("per", 2, 2)
+    x = m.node_coords()
+    k, g = 2.0 * math.pi, 1.4
+    cv = 1.0 / (g - 1.0)
+    # temperature mode
+    kap, T = 0.35, 0.02
+    uc = m.split(states.primitive_to_conserved(1.0 - 0.01 * np.sin(k * x[:, 0]), np.zeros((len(x), 3)),
+                                               np.ones(len(x))))
+    prm = scheme.Params(mu=0.0, kappa=kap, cfl=0.3, visc_dt_subtet=True)
+
+    def temperature(cells):
+        q = np.concatenate(cells)
+        p = (g - 1.0) * (q[:, 4] - 0.5 * np.sum(q[:, 1:4] ** 2, axis=1) / q[:, 0])
+        return p / q[:, 0] - 1.0
+
+    a0 = _mode(m, temperature(uc), k)
+    a1 = _mode(m, temperature(_run_to(m, uc, prm, 0.0, T)), k)
+    assert -math.log(a1 / a0) / T == pytest.approx(kap * k * k / cv, rel=0.03)
+    # longitudinal (acoustic) mode
+    mu, T, A = 0.05, 0.05, 1e-3
+    vel = np.zeros((len(x), 3))
+    vel[:, 0] = A * np.sin(k * x[:, 0])
+    uc = m.split(states.primitive_to_conserved(np.ones(len(x)), vel, np.full(len(x), 1.0 / g)))
+    prm = scheme.Params(mu=mu, kappa=0.0, cfl=0.3, visc_dt_subtet=True)
+    speed = lambda cells: (lambda q: q[:, 1] / q[:, 0])(np.concatenate(cells))  # noqa: E731
+    a0 = _mode(m, speed(uc), k)
+    ratio = _mode(m, speed(_run_to(m, uc, prm, mu, T)), k) / a0
+    b = 4.0 / 3.0 * mu * k * k
+    om = math.sqrt(k * k - 0.25 * b * b)
+    closed = math.exp(-0.5 * b * T) * (math.cos(om * T) - 0.5 * b / om * math.sin(om * T))
+    assert ratio == pytest.approx(closed, abs=3e-3)
