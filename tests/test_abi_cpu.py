@@ -106,3 +106,38 @@ def test_create_without_gpu_fails_loudly(afe):
     p = afe.afe_default_params(1, period=pm.period)
     h, st = afe.afe_mesh_create(p, pm.xyz, pm.cell_subtet_ptr, pm.subtet_vtx, pm.subtet_shift, 0, check=False)
     assert h is None and st == afe.AFE_ECUDA
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every field of the ctypes mirrors of afe_params and afe_stats sits at the offset the C
+    compiler gives it from include/afe.h, and the sizes agree."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2605_00619_gb300 import afe as mod
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = []
+    for cls in (mod.afe_params, mod.afe_stats):
+        name = cls.__name__
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "afe.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, val = line.split()
+            got[(name, field)] = int(val)
+    for cls in (mod.afe_params, mod.afe_stats):
+        name = cls.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
