@@ -422,7 +422,8 @@ def ours(args):
                    "cells": pm.n_cells, "nodes": r32["n_nodes"],
                    "dofs": dofs, "precision": "FP32 arithmetic, FP64 master state / dt / cell totals",
                    "picard_tol": 1e-6, "l2": "inputs larger than L2 (M_i^-1 alone is "
-                   f"{r32['bytes'] / 1e9:.1f} GB of device state)", "parallelism": f"{world} independent replica{'s' if world > 1 else ''}"},
+                   f"{r32['bytes'] / 1e9:.1f} GB of device state)",
+                   "parallelism": f"{world} independent replica" + ("s" if world > 1 else "")},
         "clocks": r32["clocks"],
         "gpu_launches": int(r32["launches"]),
         "status": {"fp32": r32["status"], "picard_iters_mean": r32["iters_mean"], "picard_iters_max": r32["iters_max"],
