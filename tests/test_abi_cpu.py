@@ -141,3 +141,67 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+_C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "afe.h"
+
+/* one cube [0,1]^3 split into 24 fan sub-tets: corners 0-7 (bit i of the id = coordinate
+   i), the centre 8, face centres 9-14 */
+int main(void) {
+  double xyz[15 * 3];
+  for (int v = 0; v < 8; ++v)
+    for (int d = 0; d < 3; ++d) xyz[v * 3 + d] = (v >> d) & 1;
+  for (int d = 0; d < 3; ++d) xyz[8 * 3 + d] = 0.5;
+  int64_t vtx[24 * 4];
+  int k = 0, f = 9;
+  for (int ax = 0; ax < 3; ++ax)
+    for (int side = 0; side < 2; ++side, ++f) {
+      int e1 = (ax + 1) % 3, e2 = (ax + 2) % 3;
+      for (int d = 0; d < 3; ++d) xyz[f * 3 + d] = d == ax ? side : 0.5;
+      int ring[4], uv[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+      for (int r = 0; r < 4; ++r) ring[r] = (side << ax) | (uv[r][0] << e1) | (uv[r][1] << e2);
+      for (int r = 0; r < 4; ++r, ++k) {
+        vtx[k * 4 + 0] = 8;
+        vtx[k * 4 + 1] = f;
+        vtx[k * 4 + 2] = ring[r];
+        vtx[k * 4 + 3] = ring[(r + 1) % 4];
+      }
+    }
+  int64_t ptr[2] = {0, 24};
+  afe_params p;
+  if (afe_default_params(&p, 2) != AFE_OK) return 1;
+  int64_t nodes = -1, tris = -1;
+  int st = afe_mesh_validate(&p, 15, xyz, 1, ptr, vtx, NULL, AFE_BC_TRANSMISSIVE, &nodes, &tris);
+  printf("%d %lld %lld\n", st, (long long)nodes, (long long)tris);
+  vtx[5] = vtx[4]; /* sub-tet 1: two equal vertices, zero volume */
+  st = afe_mesh_validate(&p, 15, xyz, 1, ptr, vtx, NULL, AFE_BC_TRANSMISSIVE, &nodes, &tris);
+  printf("%d %s\n", st, afe_last_error());
+  st = afe_default_params(&p, 7);
+  printf("%d %s\n", st, afe_last_error());
+  return 0;
+}
+"""
+
+
+def test_c_program_uses_the_abi(afe, tmp_path):
+    """A C program built against include/afe.h and linked to the library: default parameters,
+    validation of a one-cube mesh (P2 fan subgrid: 15 vertices + 50 subgrid edges = 65 nodes,
+    24 boundary sub-triangles), and the error path with its message."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(_C_PROGRAM)
+    exe = tmp_path / "use"
+    lib = afe.LIBPATH
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), lib,
+                    "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    assert out[0].split() == [str(afe.AFE_OK), "65", "24"]
+    assert out[1].startswith(str(afe.AFE_EMESH)) and "volume" in out[1]
+    assert out[2].startswith(str(afe.AFE_EINVAL)) and "order" in out[2]
