@@ -366,7 +366,7 @@ def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, 
 
 
 def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                      seeds: np.ndarray | None = None) -> PolyMesh:
+                      seeds: np.ndarray | None = None, thin: float = THIN) -> PolyMesh:
     """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids."""
     if seeds is None:
         seeds = jittered_seeds(n, 0.0, L, seed)
@@ -435,7 +435,7 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
         return np.stack([np.minimum(ka, kb), np.maximum(ka, kb)], 1), rs
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, L, C,
-                                                            collapse * L / n, face_key_of, h=L / n)
+                                                            collapse * L / n, face_key_of, thin=thin, h=L / n)
     if np.abs(sh).max() > 127:
         raise RuntimeError("image shift out of int8 range")
     return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
@@ -446,7 +446,7 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
 
 
 def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
-                 collapse: float = COLLAPSE, seeds: np.ndarray | None = None) -> PolyMesh:
+                 collapse: float = COLLAPSE, seeds: np.ndarray | None = None, thin: float = THIN) -> PolyMesh:
     """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids."""
     if seeds is None:
         seeds = jittered_seeds(n, lo, hi, seed)
@@ -477,7 +477,7 @@ def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
         return np.stack([k0, k1], 1), np.zeros((len(a), 3), np.int64)
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, None, C,
-                                                            collapse * h, face_key_of, h=h)
+                                                            collapse * h, face_key_of, thin=thin, h=h)
     return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
                     subtet_shift=None, periodic=False, period=(0.0, 0.0, 0.0), lo=np.full(3, lo),
                     hi=np.full(3, hi), seeds=seeds, faces_per_cell=nfaces,
@@ -496,24 +496,28 @@ def cell_centroids(pm: PolyMesh) -> np.ndarray:
 
 
 def periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                     lloyd: int = LLOYD) -> PolyMesh:
+                     lloyd: int = LLOYD, thin: float = THIN) -> PolyMesh:
     """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids, after
-    ``lloyd`` Lloyd steps of the jittered seeds and the short-edge collapse."""
+    ``lloyd`` Lloyd steps of the jittered seeds, the short-edge collapse and the thin-face
+    collapse (``thin``: the threshold in lattice spacings)."""
     seeds = jittered_seeds(n, 0.0, L, seed)
     for _ in range(lloyd):
         seeds = np.mod(cell_centroids(_periodic_voronoi(n, L, collapse=0.0, seeds=seeds)), L)
-    pm = _periodic_voronoi(n, L, seed, collapse, seeds=seeds)
+    pm = _periodic_voronoi(n, L, seed, collapse, seeds=seeds, thin=thin)
     pm.info["lloyd"] = lloyd
+    pm.info["thin"] = thin
     return pm
 
 
 def box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                lloyd: int = LLOYD) -> PolyMesh:
+                lloyd: int = LLOYD, thin: float = THIN) -> PolyMesh:
     """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids, after
-    ``lloyd`` Lloyd steps of the jittered seeds and the short-edge collapse."""
+    ``lloyd`` Lloyd steps of the jittered seeds, the short-edge collapse and the thin-face
+    collapse (``thin``: the threshold in lattice spacings)."""
     seeds = jittered_seeds(n, lo, hi, seed)
     for _ in range(lloyd):
         seeds = cell_centroids(_box_voronoi(n, lo, hi, collapse=0.0, seeds=seeds))
-    pm = _box_voronoi(n, lo, hi, seed, collapse, seeds=seeds)
+    pm = _box_voronoi(n, lo, hi, seed, collapse, seeds=seeds, thin=thin)
     pm.info["lloyd"] = lloyd
+    pm.info["thin"] = thin
     return pm
