@@ -72,8 +72,9 @@ typedef struct {
   double period[3];   /* domain period per axis; used for sub-tet vertices with image shifts   */
   int visc_dt_subtet; /* 0: the viscous term of Eq. timestep uses the cell length h_i, as printed;
                          1: it uses the cell's smallest sub-tet length min_k 6|T_k|/|dT_k|,
-                         a stricter bound under which viscous runs on subgrids with thin
-                         sub-tets stay stable (see the measurements)                          */
+                         a stricter bound: the explicit step of the viscous terms scales
+                         with the square of the smallest sub-tet size, and on subgrids with
+                         thin sub-tets viscous or limited runs stay finite only with it       */
   int h_diameter;     /* 0: h_i = 6|P_i| / |dP_i| (insphere-equivalent diameter; Sec. 4.2 leaves the
                          length open); 1: h_i = the cell's diameter, the largest distance
                          between two of its vertices (the example Sec. 4.2 names).  h_i enters
