@@ -3,7 +3,10 @@
 A request asks for ``nsteps`` CFL steps of one simulation: a mesh from a catalogue of
 resident meshes and an initial state.  Meshes are set up once (topology, mass matrices and
 their inverses: the costly part), as a pool of *slots* -- mesh handles whose state buffers
-are reused by successive requests, sized up front to a device-memory budget.  The server
+are reused by successive requests, sized up front to a device-memory budget.  With
+``elastic`` admission the pool changes with the load instead: a request whose mesh has no
+free slot gets a new one when its device footprint (dominated by the cells' M_i^-1) fits
+the budget, after evicting idle slots of other meshes, least recently used first.  The server
 loop admits arrived requests into free slots of their mesh, advances every occupied slot
 together with one launch per stage (``afe_batch_step_async``: the kernels take a table of
 meshes, so a batch of small meshes fills the GPU as one large mesh does), and retires
@@ -58,6 +61,7 @@ class Slot:
     remaining: int = 0
     order: int = 0
     xyz: Optional[np.ndarray] = None  # node coordinates (initial states given as functions)
+    last_used: float = 0.0            # when the slot last stepped (eviction order)
 
 
 class GpuEngine:
@@ -78,24 +82,59 @@ class GpuEngine:
         self.params = params
         self.stream = stream
         self.use_graph = use_graph
+        self.catalogue = dict(catalogue)
+        self.budget_bytes = budget_bytes
         self.slots: List[Slot] = []
         self.default_state = dict(default_state or {})
         self._batches: "OrderedDict[tuple, object]" = OrderedDict()
         self._max_cached = max_cached_batches
-        total = 0
+        self._footprint: Dict[str, int] = {}
+        self._next_sid = 0
+        self.device_bytes = 0
         for key, count in slots.items():
-            entry = catalogue[key]
-            pm, prm = entry if isinstance(entry, tuple) else (entry, params)
             for _ in range(count):
-                h = _afe.create_from_polymesh(pm, prm, stream)
-                nb = _afe.afe_device_bytes(h)
-                if budget_bytes is not None and total + nb > budget_bytes:
-                    _afe.afe_mesh_destroy(h)
+                if self.add_slot(key) is None:
                     break
-                total += nb
-                self.slots.append(Slot(len(self.slots), key, h, _afe.afe_num_nodes(h), nb, order=int(prm.order),
-                                       xyz=_afe.afe_get_node_coords(h)))
-        self.device_bytes = total
+
+    def _entry(self, key):
+        entry = self.catalogue[key]
+        return entry if isinstance(entry, tuple) else (entry, self.params)
+
+    def keys(self):
+        return set(self.catalogue)
+
+    def footprint(self, key) -> int:
+        """Device bytes of one slot of ``key`` (measured once, on a handle made for it)."""
+        if key not in self._footprint:
+            pm, prm = self._entry(key)
+            h = _afe.create_from_polymesh(pm, prm, self.stream)
+            self._footprint[key] = _afe.afe_device_bytes(h)
+            _afe.afe_mesh_destroy(h)
+        return self._footprint[key]
+
+    def add_slot(self, key) -> Optional[Slot]:
+        """A new slot of ``key``, or None when it would exceed the budget."""
+        pm, prm = self._entry(key)
+        h = _afe.create_from_polymesh(pm, prm, self.stream)
+        nb = _afe.afe_device_bytes(h)
+        self._footprint[key] = nb
+        if self.budget_bytes is not None and self.device_bytes + nb > self.budget_bytes:
+            _afe.afe_mesh_destroy(h)
+            return None
+        self.device_bytes += nb
+        s = Slot(self._next_sid, key, h, _afe.afe_num_nodes(h), nb, order=int(prm.order),
+                 xyz=_afe.afe_get_node_coords(h))
+        self._next_sid += 1
+        self.slots.append(s)
+        return s
+
+    def remove_slot(self, slot: Slot):
+        """Release an idle slot and every cached batch that holds it."""
+        for key in [k for k in self._batches if slot.sid in k]:
+            _afe.afe_batch_destroy(self._batches.pop(key))
+        _afe.afe_mesh_destroy(slot.handle)
+        self.slots.remove(slot)
+        self.device_bytes -= slot.nbytes
 
     # -- engine interface used by the server
     def load(self, slot: Slot, q0):
@@ -176,28 +215,46 @@ class Server:
     stepped past its nsteps and a finished slot is refilled at the next iteration.
     mode "serial": one request at a time, alone (the unbatched baseline).
     Admission is first come, first served per mesh: a request waits until a slot of its mesh
-    is free; requests for other meshes may pass it.
+    is free; requests for other meshes may pass it.  ``elastic`` (batch mode): a waiting
+    request with no free slot of its mesh gets a new slot when the engine's budget allows
+    it, after evicting idle slots of meshes nobody waits for (least recently used first).
+    The engine then needs ``keys()``, ``footprint(key)``, ``add_slot(key)``,
+    ``remove_slot(slot)``, ``device_bytes`` and ``budget_bytes``.
     """
 
     def __init__(self, engine, mode: str = "batch", max_chunk: int = 4, keep_results: bool = False,
-                 clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep):
+                 clock: Callable[[], float] = time.perf_counter, sleep: Callable[[float], None] = time.sleep,
+                 elastic: bool = False):
         if mode not in ("batch", "serial"):
             raise ValueError("mode is 'batch' or 'serial'")
+        if elastic and mode != "batch":
+            raise ValueError("elastic admission needs mode 'batch'")
         self.engine = engine
         self.mode = mode
         self.max_chunk = max(1, int(max_chunk))
         self.keep_results = keep_results
         self.clock = clock
         self.sleep = sleep
+        self.elastic = elastic
+        self.slots_added = 0
+        self.slots_evicted = 0
 
     def run(self, requests: Sequence[Request]) -> RunStats:
         pending = deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         waiting: Dict[str, deque] = {}
         slots = self.engine.slots
         mesh_keys = {s.mesh for s in slots}
-        for r in pending:
-            if r.mesh not in mesh_keys:
-                raise ValueError(f"request {r.rid}: no slot holds mesh {r.mesh!r}")
+        if self.elastic:
+            budget = self.engine.budget_bytes
+            for r in pending:
+                if r.mesh not in self.engine.keys():
+                    raise ValueError(f"request {r.rid}: mesh {r.mesh!r} is not in the catalogue")
+                if budget is not None and self.engine.footprint(r.mesh) > budget:
+                    raise ValueError(f"request {r.rid}: one slot of mesh {r.mesh!r} exceeds the budget")
+        else:
+            for r in pending:
+                if r.mesh not in mesh_keys:
+                    raise ValueError(f"request {r.rid}: no slot holds mesh {r.mesh!r}")
         t0 = self.clock()
         now = lambda: self.clock() - t0  # noqa: E731
         finished: List[Request] = []
@@ -229,6 +286,13 @@ class Server:
                     free = free_by_mesh.get(k, [])
                     while q and free:
                         self._admit(q.popleft(), free.pop(0), tnow)
+                if self.elastic:
+                    for k, q in waiting.items():
+                        while q:
+                            s = self._new_slot(k, waiting)
+                            if s is None:
+                                break
+                            self._admit(q.popleft(), s, tnow)
             running = [s for s in slots if s.busy is not None]
             if not running:
                 if pending:
@@ -249,6 +313,7 @@ class Server:
             members_total += chunk * len(running)
             tdone = now()
             for s, st in zip(running, statuses):
+                s.last_used = tdone
                 s.remaining -= chunk
                 dof_updates += 5.0 * s.n_nodes * chunk
                 if st != 0 and s.busy.status == 0:
@@ -275,6 +340,28 @@ class Server:
             failed=sum(1 for r in finished if r.status != 0),
             latencies=lat,
         )
+
+    def _new_slot(self, key, waiting) -> Optional[Slot]:
+        """A new slot of ``key`` within the budget, evicting idle slots of meshes with no
+        waiting request (least recently used first); None if it cannot fit now."""
+        eng = self.engine
+        need = eng.footprint(key)
+        budget = eng.budget_bytes
+        if budget is not None and eng.device_bytes + need > budget:
+            idle = sorted((s for s in eng.slots if s.busy is None and s.mesh != key and not waiting.get(s.mesh)),
+                          key=lambda s: (s.last_used, s.sid))
+            freeable = sum(s.nbytes for s in idle)
+            if eng.device_bytes - freeable + need > budget:
+                return None
+            for s in idle:
+                if eng.device_bytes + need <= budget:
+                    break
+                eng.remove_slot(s)
+                self.slots_evicted += 1
+        s = eng.add_slot(key)
+        if s is not None:
+            self.slots_added += 1
+        return s
 
     def _admit(self, r: Request, s: Slot, tnow: float):
         self.engine.load(s, r.q0)

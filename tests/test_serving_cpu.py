@@ -163,3 +163,149 @@ def test_poisson_arrivals_have_the_requested_rate():
     gaps = np.diff([0.0] + [r.arrival for r in reqs])
     assert np.mean(gaps) == pytest.approx(1 / 50.0, rel=0.05)
     assert all(r.nsteps == 1 and r.mesh == "a" for r in reqs)
+
+
+class ElasticFakeEngine(FakeEngine):
+    """FakeEngine whose slot pool grows and shrinks within a byte budget; footprints per mesh."""
+
+    def __init__(self, sizes, footprint, budget, **kw):
+        super().__init__([], **kw)
+        self.sizes = dict(sizes)
+        self._fp = dict(footprint)
+        self.budget_bytes = budget
+        self.device_bytes = 0
+        self.peak_bytes = 0
+        self._sid = 0
+        self.added, self.removed = [], []
+
+    def keys(self):
+        return set(self.sizes)
+
+    def footprint(self, key):
+        return self._fp[key]
+
+    def add_slot(self, key):
+        if self.device_bytes + self._fp[key] > self.budget_bytes:
+            return None
+        s = Slot(self._sid, key, None, self.sizes[key], self._fp[key])
+        self._sid += 1
+        self.slots.append(s)
+        self.device_bytes += s.nbytes
+        self.peak_bytes = max(self.peak_bytes, self.device_bytes)
+        self.added.append(key)
+        return s
+
+    def remove_slot(self, slot):
+        assert slot.busy is None, "evicted a busy slot"
+        self.slots.remove(slot)
+        self.device_bytes -= slot.nbytes
+        self.removed.append(slot.mesh)
+
+
+def test_elastic_admission_by_footprint():
+    """No slot exists up front; slots are made per request within the budget (a: 1 unit,
+    b: 3 units, budget 4) and idle slots of other meshes are evicted to make room.  Every
+    request gets exactly its steps, the budget is never exceeded and no busy slot is evicted."""
+    eng = ElasticFakeEngine({"a": 100, "b": 400}, {"a": 1, "b": 3}, 4)
+    reqs = poisson_requests(300.0, 30, ["a", "b"], [2, 3, 5], seed=3)
+    srv = Server(eng, max_chunk=2, clock=eng.clock, sleep=eng.sleep, elastic=True)
+    st = srv.run(reqs)
+    assert st.requests == 30 and st.failed == 0
+    for r in reqs:
+        assert eng.steps_of[r.rid] == r.nsteps
+    assert eng.peak_bytes <= 4
+    assert srv.slots_added == len(eng.added) and srv.slots_evicted == len(eng.removed) > 0
+    assert {"a", "b"} <= set(eng.added)
+    for sids, _ in eng.batches:  # a batch never holds more than the budget allows
+        assert len(sids) <= 4
+
+
+def test_elastic_admission_rejects_what_can_never_fit():
+    eng = ElasticFakeEngine({"a": 100, "c": 900}, {"a": 1, "c": 9}, 4)
+    with pytest.raises(ValueError, match="exceeds the budget"):
+        Server(eng, clock=eng.clock, sleep=eng.sleep, elastic=True).run([Request(0, "c", 1, 0.0)])
+    with pytest.raises(ValueError, match="not in the catalogue"):
+        Server(eng, clock=eng.clock, sleep=eng.sleep, elastic=True).run([Request(0, "z", 1, 0.0)])
+    with pytest.raises(ValueError, match="elastic"):
+        Server(eng, mode="serial", elastic=True)
+
+
+class _FakeLib:
+    """Stands in for the C-ABI binding under GpuEngine (host logic only): handles are
+    integers, a mesh's device bytes are given per catalogue object, batches are recorded."""
+
+    def __init__(self, nbytes):
+        self.nbytes = nbytes
+        self.live = {}
+        self.batches = {}
+        self._id = 0
+        self.AFE_OK = 0
+
+    def create_from_polymesh(self, pm, prm, stream=0):
+        self._id += 1
+        self.live[self._id] = pm
+        return self._id
+
+    def afe_device_bytes(self, h):
+        return self.nbytes[self.live[h]]
+
+    def afe_num_nodes(self, h):
+        return 10
+
+    def afe_get_node_coords(self, h):
+        return np.zeros((10, 3))
+
+    def afe_mesh_destroy(self, h):
+        del self.live[h]
+
+    def afe_set_state(self, h, q):
+        assert h in self.live
+
+    def afe_batch_create(self, handles, stream=0):
+        for h in handles:
+            assert h in self.live
+        self._id += 1
+        self.batches[self._id] = list(handles)
+        return self._id
+
+    def afe_batch_destroy(self, b):
+        del self.batches[b]
+
+    def afe_batch_step_async(self, b, dt, n, use_graph):
+        for h in self.batches[b]:
+            assert h in self.live, "batch holds a destroyed handle"
+
+    def afe_batch_sync(self, b, n, check=True):
+        return 0, [0] * n
+
+
+def test_gpu_engine_host_logic_with_elastic_admission(monkeypatch):
+    """GpuEngine's slot bookkeeping over a fake binding: slots made and released within the
+    budget, cached batches that hold an evicted slot destroyed with it, and no handle leaked."""
+    from types import SimpleNamespace
+
+    from paper_2605_00619_gb300 import serving
+    fake = _FakeLib({"mesh-a": 100, "mesh-b": 300})
+    monkeypatch.setattr(serving, "_afe", fake)
+    prm = SimpleNamespace(order=2)
+    eng = serving.GpuEngine({"a": "mesh-a", "b": "mesh-b"}, {"a": 1}, params=prm, budget_bytes=400,
+                            default_state={"a": np.zeros((10, 5)), "b": np.zeros((10, 5))})
+    assert len(eng.slots) == 1 and eng.device_bytes == 100
+    assert eng.footprint("b") == 300 and len(fake.live) == 1      # measured on a handle made and freed
+    reqs = poisson_requests(1000.0, 24, ["a", "b"], [1, 2, 3], seed=5)
+    clock = {"t": 0.0}
+
+    def tick():
+        clock["t"] += 1e-3
+        return clock["t"]
+
+    srv = serving.Server(eng, max_chunk=2, clock=tick, sleep=lambda dt: clock.__setitem__("t", clock["t"] + dt),
+                         elastic=True)
+    st = srv.run(reqs)
+    assert st.requests == 24 and st.failed == 0
+    assert eng.device_bytes <= 400 and srv.slots_evicted > 0
+    assert len(fake.live) == len(eng.slots)
+    for b, handles in fake.batches.items():
+        assert all(h in fake.live for h in handles)
+    eng.close()
+    assert not fake.live and not fake.batches
