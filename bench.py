@@ -75,6 +75,10 @@ def _args():
     ap.add_argument("--serve-rate", type=float, default=50.0, help="offered load, requests per second")
     ap.add_argument("--serve-steps", type=int, default=20, help="CFL steps per request")
     ap.add_argument("--serve-slots", type=int, default=4, help="slots per catalogue entry (mesh, N)")
+    ap.add_argument("--serve-elastic", type=float, default=None, metavar="BYTES",
+                    help="admit by device footprint within BYTES instead of fixed slot pools")
+    ap.add_argument("--serve-limiter", action="store_true",
+                    help="explosion requests with the limiter and the sub-tet viscous time step")
     return ap.parse_args()
 
 
@@ -506,9 +510,12 @@ def serve(args):
     unit cube and the box [-1,1]^3, 8^3 and 12^3 seeds -- with N uniform in {1, 2, 3}; the
     periodic meshes carry the density wave, the box meshes a spherical explosion smoothed
     over 1.5 lattice spacings with a random centre in [-0.5,0.5]^3 and pressure ratio in
-    [2, 10] (no limiter: with the artificial viscosity these runs diverge within a few steps
-    on the fan-subgrid meshes); each
-    request runs ``--serve-steps`` CFL steps.  Arrivals are a Poisson process of
+    [2, 10] (no limiter by default: with the artificial viscosity and the printed viscous
+    time step these runs diverge within a few steps on the fan-subgrid meshes;
+    ``--serve-limiter`` turns the limiter on together with the sub-tet viscous time step); each
+    request runs ``--serve-steps`` CFL steps.  ``--serve-elastic BYTES`` starts the batched
+    server with no slots and admits requests by device footprint within BYTES (idle slots of
+    other meshes evicted least recently used first) instead of fixed pools.  Arrivals are a Poisson process of
     ``--serve-rate`` per second.  The batched server (FP32 form; every occupied slot advanced
     together, one launch per stage and order, a CUDA graph per batch) is timed against the
     serial server running the same requests one at a time in the plain FP64 form.  Reported:
@@ -532,13 +539,16 @@ def serve(args):
 
     def params(kind, N, prec):
         fp32 = prec == afe.AFE_FP32
+        extra = dict(limiter=1, visc_dt_subtet=1) if kind == "b" and args.serve_limiter else {}
         return afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
-                                      picard_max=128 if fp32 else 64, cfl=STABLE_CFL[N])
+                                      picard_max=128 if fp32 else 64, cfl=STABLE_CFL[N], **extra)
 
     keys = [f"{mk}_N{N}" for mk in sorted(meshes) for N in (1, 2, 3)]
     cat32 = {k: (meshes[k.split("_")[0]], params(k[0], int(k[-1]), afe.AFE_FP32)) for k in keys}
     cat64 = {k: (meshes[k.split("_")[0]], params(k[0], int(k[-1]), afe.AFE_FP64)) for k in keys}
-    eng = GpuEngine(cat32, {k: args.serve_slots for k in keys})
+    elastic = args.serve_elastic is not None
+    eng = (GpuEngine(cat32, {}, budget_bytes=int(args.serve_elastic)) if elastic
+           else GpuEngine(cat32, {k: args.serve_slots for k in keys}))
     ser = GpuEngine(cat64, {k: 1 for k in keys})
 
     rng = np.random.default_rng(12345)
@@ -559,12 +569,13 @@ def serve(args):
             out.append(Request(i, k, args.serve_steps, t, q0=ic))
         return out
 
-    Server(eng).run(make_requests(len(eng.slots), 0.0))            # warm-up: graphs, caches
+    Server(eng, elastic=elastic).run(make_requests(len(keys) if elastic else len(eng.slots), 0.0))  # warm-up
     Server(ser, mode="serial").run(make_requests(len(keys), 0.0))
     reqs = make_requests(args.serve_requests, args.serve_rate)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    sb = Server(eng, max_chunk=8).run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
+    srv = Server(eng, max_chunk=8, elastic=elastic)
+    sb = srv.run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
     clk = clocks.stop()
     ss = Server(ser, mode="serial").run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
     out = {
@@ -581,7 +592,10 @@ def serve(args):
                                f"{args.serve_steps} CFL steps each; meshes periodic/box {sizes[0]}^3 and "
                                f"{sizes[1]}^3, N in {{1,2,3}}; density wave (periodic) or smoothed spherical "
                                f"explosion, pressure ratio 2-10 (box)",
-                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes},
+                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes,
+                   "admission": (f"elastic within {int(args.serve_elastic)} bytes: {srv.slots_added} slots made, "
+                                 f"{srv.slots_evicted} evicted") if elastic else "fixed slot pools",
+                   "limiter_on_explosions": bool(args.serve_limiter)},
     }
     eng.close()
     ser.close()
