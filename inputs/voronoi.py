@@ -57,6 +57,9 @@ COLLAPSE = 0.25
 THIN = 0.08
 # Lloyd steps applied to the jittered seeds (each moves a seed to its cell's centroid)
 LLOYD = 4
+# fan triangles whose plane passes closer than FLAT * (lattice spacing) to the cell centre
+# (flat sub-tets of warped faces) mark the face like a thin one; 0 turns the test off
+FLAT = 0.0
 
 
 @dataclass
@@ -278,18 +281,24 @@ def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
     return xyz, sub_ptr, vtx, sh
 
 
-def _thin_faces(xyz, vtx, sh, L, h, thin):
-    """Fan sub-tets whose face centre lies within thin*h of the line of their face edge."""
+def _thin_faces(xyz, vtx, sh, L, h, thin, flatness=0.0):
+    """Fan sub-tets whose face centre lies within thin*h of the line of their face edge, or
+    (flatness > 0) whose fan triangle's plane passes within flatness*h of the cell centre."""
     Lf = 0.0 if L is None else L
     P = xyz[vtx] + sh * Lf
     e = P[:, 3] - P[:, 2]
     u = e / np.linalg.norm(e, axis=1)[:, None]
     w = P[:, 1] - P[:, 2]
     dist = np.linalg.norm(w - u * np.einsum("ij,ij->i", w, u)[:, None], axis=1)
-    return np.nonzero(dist < thin * h)[0]
+    bad = dist < thin * h
+    if flatness > 0:
+        nrm = np.cross(P[:, 2] - P[:, 1], P[:, 3] - P[:, 1])
+        height = np.abs(np.einsum("ij,ij->i", P[:, 0] - P[:, 1], nrm)) / np.linalg.norm(nrm, axis=1)
+        bad |= height < flatness * h
+    return np.nonzero(bad)[0]
 
 
-def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, h=0.0):
+def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, h=0.0, flatness=FLAT):
     exclude: set = set()
     force: set = set()
     anchor: set = set()
@@ -341,7 +350,7 @@ def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, 
             continue
         if tol > 0 and thin > 0:
             # thin faces: collapse the shortest edge of every face with a thin fan triangle
-            bad = _thin_faces(xyz, vtx, sh, L, h, thin)
+            bad = _thin_faces(xyz, vtx, sh, L, h, thin, flatness)
             added = False
             if len(bad):
                 cnt2 = np.diff(ptr2)
@@ -366,7 +375,7 @@ def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, 
 
 
 def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                      seeds: np.ndarray | None = None, thin: float = THIN) -> PolyMesh:
+                      seeds: np.ndarray | None = None, thin: float = THIN, flatness: float = FLAT) -> PolyMesh:
     """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids."""
     if seeds is None:
         seeds = jittered_seeds(n, 0.0, L, seed)
@@ -435,7 +444,8 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
         return np.stack([np.minimum(ka, kb), np.maximum(ka, kb)], 1), rs
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, L, C,
-                                                            collapse * L / n, face_key_of, thin=thin, h=L / n)
+                                                            collapse * L / n, face_key_of, thin=thin, h=L / n,
+                                                            flatness=flatness)
     if np.abs(sh).max() > 127:
         raise RuntimeError("image shift out of int8 range")
     return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
@@ -446,7 +456,8 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
 
 
 def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
-                 collapse: float = COLLAPSE, seeds: np.ndarray | None = None, thin: float = THIN) -> PolyMesh:
+                 collapse: float = COLLAPSE, seeds: np.ndarray | None = None, thin: float = THIN,
+                 flatness: float = FLAT) -> PolyMesh:
     """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids."""
     if seeds is None:
         seeds = jittered_seeds(n, lo, hi, seed)
@@ -477,7 +488,8 @@ def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
         return np.stack([k0, k1], 1), np.zeros((len(a), 3), np.int64)
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, None, C,
-                                                            collapse * h, face_key_of, thin=thin, h=h)
+                                                            collapse * h, face_key_of, thin=thin, h=h,
+                                                            flatness=flatness)
     return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
                     subtet_shift=None, periodic=False, period=(0.0, 0.0, 0.0), lo=np.full(3, lo),
                     hi=np.full(3, hi), seeds=seeds, faces_per_cell=nfaces,
@@ -496,28 +508,30 @@ def cell_centroids(pm: PolyMesh) -> np.ndarray:
 
 
 def periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                     lloyd: int = LLOYD, thin: float = THIN) -> PolyMesh:
+                     lloyd: int = LLOYD, thin: float = THIN, flat: float = FLAT) -> PolyMesh:
     """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids, after
     ``lloyd`` Lloyd steps of the jittered seeds, the short-edge collapse and the thin-face
     collapse (``thin``: the threshold in lattice spacings)."""
     seeds = jittered_seeds(n, 0.0, L, seed)
     for _ in range(lloyd):
         seeds = np.mod(cell_centroids(_periodic_voronoi(n, L, collapse=0.0, seeds=seeds)), L)
-    pm = _periodic_voronoi(n, L, seed, collapse, seeds=seeds, thin=thin)
+    pm = _periodic_voronoi(n, L, seed, collapse, seeds=seeds, thin=thin, flatness=flat)
     pm.info["lloyd"] = lloyd
     pm.info["thin"] = thin
+    pm.info["flat"] = flat
     return pm
 
 
 def box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                lloyd: int = LLOYD, thin: float = THIN) -> PolyMesh:
+                lloyd: int = LLOYD, thin: float = THIN, flat: float = FLAT) -> PolyMesh:
     """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids, after
     ``lloyd`` Lloyd steps of the jittered seeds, the short-edge collapse and the thin-face
     collapse (``thin``: the threshold in lattice spacings)."""
     seeds = jittered_seeds(n, lo, hi, seed)
     for _ in range(lloyd):
         seeds = cell_centroids(_box_voronoi(n, lo, hi, collapse=0.0, seeds=seeds))
-    pm = _box_voronoi(n, lo, hi, seed, collapse, seeds=seeds, thin=thin)
+    pm = _box_voronoi(n, lo, hi, seed, collapse, seeds=seeds, thin=thin, flatness=flat)
     pm.info["lloyd"] = lloyd
     pm.info["thin"] = thin
+    pm.info["flat"] = flat
     return pm
