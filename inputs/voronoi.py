@@ -31,6 +31,9 @@ Recipe
   at N = 2 is 0.27; with four steps and 0.25 it is 0.44).
 * Thin faces: a face whose centre lies closer than ``THIN`` times the lattice
   spacing to the line of one of its edges has its shortest edge collapsed too.
+* Flat sub-tets: likewise a face one of whose fan triangles lies in a plane passing closer
+  than ``FLAT`` times the lattice spacing to the cell centre (a face warped by the
+  collapse); such a sub-tet makes the ADER step locally unstable at the CFL numbers used.
 * Fan subgrid: each cell is split by joining its centre (the mean of its
   vertices) to a fan triangulation of each face about the face centre (the mean
   of the face's vertices): one sub-tet per face edge.
@@ -59,7 +62,7 @@ THIN = 0.08
 LLOYD = 4
 # fan triangles whose plane passes closer than FLAT * (lattice spacing) to the cell centre
 # (flat sub-tets of warped faces) mark the face like a thin one; 0 turns the test off
-FLAT = 0.0
+FLAT = 0.1
 
 
 @dataclass
