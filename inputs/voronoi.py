@@ -245,8 +245,9 @@ def _collapse(pos, ptr, fv, fs, L, tol, exclude, force=(), anchor=()):
     return new_pos, ptr2, ids[keep_e], sh[keep_e], np.nonzero(keep_f)[0], merges, members, new_id
 
 
-def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
-    """Face centres, cell centres and fan sub-tets; raises _Fold on a non-positive sub-tet."""
+def _fan(pos, cells, ptr, fv, fs, L, C, face_key, allow_fold=False):
+    """Face centres, cell centres and fan sub-tets; raises _Fold on a non-positive sub-tet
+    unless ``allow_fold`` (sub-tets used only for cell centroids)."""
     Lf = 0.0 if L is None else L
     cnt = np.diff(ptr)
     X = pos[fv] + fs * Lf
@@ -276,7 +277,7 @@ def _fan(pos, cells, ptr, fv, fs, L, C, face_key):
     P = xyz[vtx] + sh * Lf
     det = np.linalg.det(np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]], -1))
     bad = np.nonzero(~(det > 0))[0]
-    if len(bad):
+    if len(bad) and not allow_fold:
         near = sorted({int(v) for j in bad for v in (fv[j], fv[nxt[j]])})
         face = sorted({int(v) for f in set(fidx[bad].tolist()) for v in fv[ptr[f]:ptr[f + 1]]})
         raise _Fold(near, face)
@@ -301,7 +302,8 @@ def _thin_faces(xyz, vtx, sh, L, h, thin, flatness=0.0):
     return np.nonzero(bad)[0]
 
 
-def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, h=0.0, flatness=FLAT):
+def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, h=0.0, flatness=FLAT,
+              allow_fold=False):
     exclude: set = set()
     force: set = set()
     anchor: set = set()
@@ -318,7 +320,8 @@ def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, 
         try:
             kc = cells[keep]
             kn = nbrs[keep]
-            xyz, sub_ptr, vtx, sh = _fan(new_pos, kc, ptr2, fv2, fs2, L, C, lambda f: face_key_of(kc[f], kn[f]))
+            xyz, sub_ptr, vtx, sh = _fan(new_pos, kc, ptr2, fv2, fs2, L, C, lambda f: face_key_of(kc[f], kn[f]),
+                                         allow_fold)
         except _Fold as e:
             # first place a merged vertex at the folded edges at one of its members instead of
             # the members' mean (a short edge collapses onto an end point); when every choice
@@ -378,7 +381,8 @@ def _assemble(pos, cells, ptr, fv, fs, nbrs, L, C, tol, face_key_of, thin=THIN, 
 
 
 def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = COLLAPSE,
-                      seeds: np.ndarray | None = None, thin: float = THIN, flatness: float = FLAT) -> PolyMesh:
+                      seeds: np.ndarray | None = None, thin: float = THIN, flatness: float = FLAT,
+                      allow_fold: bool = False) -> PolyMesh:
     """Periodic jittered-lattice Voronoi mesh of ``[0, L)^3`` with fan subgrids."""
     if seeds is None:
         seeds = jittered_seeds(n, 0.0, L, seed)
@@ -448,7 +452,7 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, L, C,
                                                             collapse * L / n, face_key_of, thin=thin, h=L / n,
-                                                            flatness=flatness)
+                                                            flatness=flatness, allow_fold=allow_fold)
     if np.abs(sh).max() > 127:
         raise RuntimeError("image shift out of int8 range")
     return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
@@ -460,7 +464,7 @@ def _periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = C
 
 def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
                  collapse: float = COLLAPSE, seeds: np.ndarray | None = None, thin: float = THIN,
-                 flatness: float = FLAT) -> PolyMesh:
+                 flatness: float = FLAT, allow_fold: bool = False) -> PolyMesh:
     """Jittered-lattice Voronoi mesh of the box ``[lo, hi]^3`` with fan subgrids."""
     if seeds is None:
         seeds = jittered_seeds(n, lo, hi, seed)
@@ -492,7 +496,7 @@ def _box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0,
 
     xyz, sub_ptr, vtx, sh, merges, nvor, nfaces = _assemble(pos, cells, ptr, fv, fs, nbrs, None, C,
                                                             collapse * h, face_key_of, thin=thin, h=h,
-                                                            flatness=flatness)
+                                                            flatness=flatness, allow_fold=allow_fold)
     return PolyMesh(xyz=xyz, cell_subtet_ptr=sub_ptr.astype(np.int64), subtet_vtx=vtx.astype(np.int64),
                     subtet_shift=None, periodic=False, period=(0.0, 0.0, 0.0), lo=np.full(3, lo),
                     hi=np.full(3, hi), seeds=seeds, faces_per_cell=nfaces,
@@ -517,7 +521,8 @@ def periodic_voronoi(n: int, L: float = 1.0, seed: int = 0, collapse: float = CO
     collapse (``thin``: the threshold in lattice spacings)."""
     seeds = jittered_seeds(n, 0.0, L, seed)
     for _ in range(lloyd):
-        seeds = np.mod(cell_centroids(_periodic_voronoi(n, L, collapse=0.0, seeds=seeds)), L)
+        # (raw cells: a degenerate face may give a flat or folded fan sub-tet, harmless here)
+        seeds = np.mod(cell_centroids(_periodic_voronoi(n, L, collapse=0.0, seeds=seeds, allow_fold=True)), L)
     pm = _periodic_voronoi(n, L, seed, collapse, seeds=seeds, thin=thin, flatness=flat)
     pm.info["lloyd"] = lloyd
     pm.info["thin"] = thin
@@ -532,7 +537,7 @@ def box_voronoi(n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0, collap
     collapse (``thin``: the threshold in lattice spacings)."""
     seeds = jittered_seeds(n, lo, hi, seed)
     for _ in range(lloyd):
-        seeds = cell_centroids(_box_voronoi(n, lo, hi, collapse=0.0, seeds=seeds))
+        seeds = cell_centroids(_box_voronoi(n, lo, hi, collapse=0.0, seeds=seeds, allow_fold=True))
     pm = _box_voronoi(n, lo, hi, seed, collapse, seeds=seeds, thin=thin, flatness=flat)
     pm.info["lloyd"] = lloyd
     pm.info["thin"] = thin
