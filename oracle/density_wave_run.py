@@ -7,7 +7,10 @@ shortened to land on t = 0.1) and prints the error in rho against the exact solu
 volume-weighted nodal L2 norm sqrt(sum_i |P_i| mean_{n in P_i} e_n^2) and the max norm, the
 numbers the GPU accuracy study reports for the same mesh, order and CFL.
 
-    python -m oracle.density_wave_run --n 8 --N 2 --cfl 0.2 [--thin 0.04]
+    python -m oracle.density_wave_run --n 8 --N 2 --cfl 0.2 [--thin 0.04] [--flat 0]
+
+The stored result tests/golden/density_wave_8c_N2.json was written by this command with
+the defaults (``> tests/golden/density_wave_8c_N2.json``).
 """
 from __future__ import annotations
 
@@ -19,14 +22,14 @@ import time
 import numpy as np
 
 from inputs import states
-from inputs.voronoi import THIN, periodic_voronoi
+from inputs.voronoi import FLAT, THIN, periodic_voronoi
 
 from . import scheme
 from .mesh import from_polymesh
 
 
-def run(n, N, cfl, t_end=0.1, thin=THIN):
-    m = from_polymesh(periodic_voronoi(n, thin=thin), N)
+def run(n, N, cfl, t_end=0.1, thin=THIN, flat=FLAT):
+    m = from_polymesh(periodic_voronoi(n, thin=thin, flat=flat), N)
     x = m.node_coords()
     uc = m.split(states.density_wave(x))
     prm = scheme.Params(cfl=cfl)
@@ -37,7 +40,7 @@ def run(n, N, cfl, t_end=0.1, thin=THIN):
         uc, _ = scheme.step(m, uc, prm, dt=dt)
     e2 = (np.concatenate(uc)[:, 0] - states.density_wave(x, t=t_end)[:, 0]) ** 2
     l2 = math.sqrt(sum(c.vol * float(np.mean(e2[m.node_ptr[i]:m.node_ptr[i + 1]])) for i, c in enumerate(m.cells)))
-    return {"n": n, "N": N, "cfl": cfl, "thin": thin, "steps": nsteps, "dt": dt, "l2_rho": l2,
+    return {"n": n, "N": N, "cfl": cfl, "thin": thin, "flat": flat, "steps": nsteps, "dt": dt, "l2_rho": l2,
             "linf_rho": float(np.sqrt(e2.max())), "seconds": time.perf_counter() - t0}
 
 
@@ -47,5 +50,6 @@ if __name__ == "__main__":
     ap.add_argument("--N", type=int, default=2)
     ap.add_argument("--cfl", type=float, default=0.2)
     ap.add_argument("--thin", type=float, default=THIN)
+    ap.add_argument("--flat", type=float, default=FLAT)
     a = ap.parse_args()
-    print(json.dumps(run(a.n, a.N, a.cfl, thin=a.thin)))
+    print(json.dumps(run(a.n, a.N, a.cfl, thin=a.thin, flat=a.flat)))
