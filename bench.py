@@ -40,12 +40,14 @@ METRIC = "DOF-updates/s per ADER-DG step"
 # N = 3 within 8 steps at 0.3 and after ~30 at 0.2.
 STABLE_CFL = {1: 0.3, 2: 0.2, 3: 0.15}
 PAPER_CFL = 0.3
+# CFL steps after which both forms' accuracy is compared in the throughput run
+L2_STEPS = 3
 
-# DRAM bytes (read + write) of one predictor_f32_kernel<3> launch per cell, from the ncu
-# capture summarised in profiles/step_kernels_density_wave_12c_N3.md (907 MB over 1728 cells
-# of the density-wave workload): the fixed-point iterations re-read M_i^-1 from L2, so the
-# traffic grows with the cells, not with the iterations.  Valid for that kernel version only.
-PREDICTOR_N3_DRAM_BYTES_PER_CELL = (865.222656e6 + 42.158848e6) / 1728
+# DRAM bytes (read + write) of one predictor_f32_kernel<3> launch per cell of the density-wave
+# workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 12^3 launch
+# of the current kernel; None until that capture exists.  The fixed-point iterations re-read
+# M_i^-1 from L2, so the traffic grows with the cells, not with the iterations.
+PREDICTOR_N3_DRAM_BYTES_PER_CELL = None
 UNIT = "DOF-updates/s"
 
 
@@ -239,16 +241,20 @@ class ClockSampler:
 
 
 def predictor_model(node_ptr, sub_ptr, iters, N, real_bytes):
-    """Algorithmic flops and bytes of one predictor launch (the dominant kernel).
+    """Algorithmic work of one predictor launch (the dominant kernel), split by the pipe the
+    design puts it on.
 
     Per cell and fixed-point iteration, with Np = (N+1)(N+2)(N+3)/6, Nt = N+1, S sub-tets,
-    N_i nodes: flux + 3x3 pre-contraction 150 flop per (sub-tet, time, node); the reference
-    stiffness contraction 2*3*Np flop per (sub-tet, time, node, variable); the agglomeration
-    1 flop per incidence and variable; the inverse-mass apply 2 N_i^2 (5 Nt); the update
-    2 Nt per (node, time, variable).  Epilogue: one more flux pass and the volume term.
-    Bytes (the method's minimum): the dense M_i^-1 once per step (rows of 16 ceil(N_i/16) + 8
-    words), the state, the sub-tet records and the outputs once; the variant that streams
-    M_i^-1 from HBM in every fixed-point iteration is returned beside it.
+    N_i nodes.  Dense contractions (tensor cores): the reference-stiffness contraction,
+    2 * 3 Np flop per (sub-tet, time, node, variable), and the inverse-mass apply
+    2 N_i^2 (5 Nt); the epilogue's volume-term contraction once per step.  Pointwise work
+    (FP32 FMA pipe): flux and 3x3 pre-contraction 150 flop per (sub-tet, time, node), the
+    agglomeration 1 flop per incidence and variable, the update 2 Nt per (node, time,
+    variable), and the epilogue's flux pass.  Bytes (the method's minimum): M_i^-1 once per
+    step (N_i^2 words; row padding is storage, not work), the state, the sub-tet records and
+    the outputs once; the variant that streams M_i^-1 from HBM in every fixed-point
+    iteration is returned beside it.  Returns (contraction flops, pointwise flops, bytes,
+    streamed bytes).
     """
     import numpy as np
     Np = (N + 1) * (N + 2) * (N + 3) // 6
@@ -256,14 +262,51 @@ def predictor_model(node_ptr, sub_ptr, iters, N, real_bytes):
     Ni = np.diff(node_ptr).astype(np.float64)
     S = np.diff(sub_ptr).astype(np.float64)
     it = iters.astype(np.float64)
-    per_it = S * Nt * Np * (150 + 5 * 6 * Np + 5) + 2 * Ni * Ni * 5 * Nt + Ni * Nt * 5 * 2 * Nt
-    epi = S * Np * Nt * 150 + S * Np * 5 * 6 * Np + S * Np * 5
-    flops = float(np.sum(it * per_it + epi))
-    LD = np.ceil(Ni / 16) * 16 + 8
+    con_it = S * Nt * Np * 5 * 6 * Np + 2 * Ni * Ni * 5 * Nt
+    pw_it = S * Nt * Np * (150 + 5) + Ni * Nt * 5 * 2 * Nt
+    con_epi = S * Np * 5 * 6 * Np
+    pw_epi = S * Np * Nt * 150 + S * Np * 5
+    f_con = float(np.sum(it * con_it + con_epi))
+    f_pw = float(np.sum(it * pw_it + pw_epi))
     once = Ni * 5 * 8 + S * (10 * 4 + Np * 2) + Ni * 5 * real_bytes
-    bytes_min = float(np.sum(Ni * LD * real_bytes + once))
-    bytes_streamed = float(np.sum(it * Ni * LD * real_bytes + once))
-    return flops, bytes_min, bytes_streamed
+    bytes_min = float(np.sum(Ni * Ni * real_bytes + once))
+    bytes_streamed = float(np.sum(it * Ni * Ni * real_bytes + once))
+    return f_con, f_pw, bytes_min, bytes_streamed
+
+
+def predictor_roofline(f_con, f_pw, abytes, ms, peaks):
+    """Time-based roofline of one predictor launch against the pipes the design assigns:
+    contractions on the tensor cores as 3xTF32 (the TF32 dense peak, taken as half the
+    measured BF16 burst peak by the nominal 1:2 ratio, divided by the three products of
+    the split), pointwise work on the FP32 FMA pipe (152 SMs x 128 lanes x 2 flop x the
+    maximum SM clock), bytes at the measured HBM copy bandwidth.  The roofline time is
+    max(t_hbm, t_tensor + t_fma); the main fields follow the bound that sets it."""
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    sm_max = peaks.get("sm_max_mhz") or 2070.0
+    tf32 = bf16 / 2.0
+    tensor_eff = tf32 / 3.0
+    fma = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    t = ms / 1e3
+    t_hbm = abytes / (hbm * 1e9)
+    t_ten = f_con / (tensor_eff * 1e12)
+    t_fma = f_pw / (fma * 1e12)
+    t_roof = max(t_hbm, t_ten + t_fma)
+    if t_hbm >= t_ten + t_fma:
+        ach = abytes / t / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+               "peak_note": "of measured (HBM copy bandwidth)"}
+    else:
+        ach = f_con / t / 1e12
+        out = {"bound": "tensor", "achieved": ach, "peak": tensor_eff, "unit": "TFLOP/s", "frac": ach / tensor_eff,
+               "peak_note": "3xTF32 effective: half the measured BF16 burst peak (nominal TF32:BF16 ratio) / 3"}
+    out.update({"frac_roofline_time": t_roof / t, "roofline_ms": t_roof * 1e3, "measured_ms": ms,
+                "pipes_ms": {"hbm": t_hbm * 1e3, "tensor_3xtf32": t_ten * 1e3, "fp32_fma": t_fma * 1e3},
+                "peaks": {"hbm_gbs": hbm, "tf32_tflops": tf32, "tensor_3xtf32_tflops": tensor_eff,
+                          "fp32_fma_tflops": fma},
+                "algorithmic_flops_contraction": f_con, "algorithmic_flops_pointwise": f_pw,
+                "algorithmic_bytes": abytes})
+    return out
 
 
 class RankReducer:
@@ -331,6 +374,10 @@ def ours(args):
         pm = periodic_voronoi(args.n, seed=rank)
     stream = torch.cuda.Stream()
     sid = stream.cuda_stream
+    sub = pm.subtet_coords()
+    cell_vol = np.bincount(np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr)),
+                           weights=np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0, minlength=pm.n_cells)
+    del sub
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -360,7 +407,24 @@ def ours(args):
         else:
             u0 = states.density_wave(x)
         afe.afe_set_state(h, u0)
-        afe.afe_step_async(h, 0.0, warmup)
+        # accuracy at equal steps: the density wave after L2_STEPS CFL steps against the exact
+        # solution, taken inside the warm-up (FP32 form) or after the timed steps (FP64 form)
+        l2_rec = None
+
+        def density_l2():
+            st_ = afe.afe_get_stats(h)
+            q_ = afe.afe_get_state(h)
+            e2 = (q_[:, 0] - states.density_wave(x, t=st_.t)[:, 0]) ** 2
+            per_cell = np.add.reduceat(e2, node_ptr[:-1]) / np.diff(node_ptr)
+            return {"steps": int(st_.steps), "t": st_.t, "l2_rho": float(np.sqrt(np.sum(cell_vol * per_cell))),
+                    "rho": q_[:, 0].copy()}
+
+        pre = L2_STEPS if (args.workload == "density" and warmup >= L2_STEPS) else 0
+        if pre:
+            afe.afe_step_async(h, 0.0, pre)
+            afe.afe_sync(h, check=False)
+            l2_rec = density_l2()
+        afe.afe_step_async(h, 0.0, warmup - pre)
         st = afe.afe_sync(h, check=False)
         barrier()
         afe.afe_set_profiling(h, True)
@@ -385,11 +449,13 @@ def ours(args):
         afe.afe_set_profiling(h, False)
         stats = afe.afe_get_stats(h)
         launches = stats.kernel_launches - launches0
+        if l2_rec is None and args.workload == "density" and stats.steps == L2_STEPS:
+            l2_rec = density_l2()
         _, iters, _, _ = afe.afe_get_diagnostics(h, pm.n_cells, qbar=False)
         rec = dict(status=[st, st2], ms=ms, wall=wall, stage_ms=(stage_ms / max(nst, 1)).tolist(), clocks=clk,
                    n_nodes=n_nodes, launches=launches, iters_mean=float(iters.mean()), iters_max=int(iters.max()),
-                   nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h))
-        rec["flops"], rec["abytes"], rec["abytes_streamed"] = predictor_model(
+                   nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h), l2=l2_rec)
+        rec["f_con"], rec["f_pw"], rec["abytes"], rec["abytes_streamed"] = predictor_model(
             node_ptr, pm.cell_subtet_ptr, iters, args.order, 4 if prec == afe.AFE_FP32 else 8)
         if e2e:
             # end to end through the public API, host buffers: per step the state goes up from
@@ -438,30 +504,15 @@ def ours(args):
         e2e_wall = max_over_ranks(r32["e2e_wall"])
         out["e2e"] = {"value": total_dofs / e2e_wall, "unit": UNIT, "h2d_bytes_per_step": r32["n_nodes"] * 5 * 8,
                       "d2h_bytes_per_step": r32["n_nodes"] * 5 * 8}
-    # roofline of the dominant kernel (the predictor), FP32 CUDA-core arithmetic vs HBM
+    # roofline of the dominant kernel (the predictor), by the pipes the design assigns
     pred_ms = r32["stage_ms"][1]
-    sm_max = (peaks.get("sm_max_mhz") or 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA units x clock
-    hbm = peaks.get("hbm_gbs") or 6800.0
-    t_alu = r32["flops"] / (fp32_peak * 1e12)
-    t_hbm = r32["abytes"] / (hbm * 1e9)
-    if t_alu >= t_hbm:
-        ach = r32["flops"] / (pred_ms / 1e3) / 1e12
-        out["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                           "frac": ach / fp32_peak, "traffic": None,
-                           "kernel": f"predictor_f32_kernel<{args.order}>",
-                           "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"}
-    else:
-        ach = r32["abytes"] / (pred_ms / 1e3) / 1e9
-        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                           "traffic": None, "kernel": f"predictor_f32_kernel<{args.order}>", "peak_note": "of measured"}
-    out["roofline"]["algorithmic_flops"] = r32["flops"]
-    out["roofline"]["algorithmic_bytes"] = r32["abytes"]
+    out["roofline"] = predictor_roofline(r32["f_con"], r32["f_pw"], r32["abytes"], pred_ms, peaks)
+    out["roofline"]["kernel"] = f"predictor_f32_kernel<{args.order}>"
+    out["roofline"]["traffic"] = None
     out["roofline"]["algorithmic_bytes_streamed_per_iteration"] = r32["abytes_streamed"]
-    if args.order == 3 and args.workload == "density":
+    if args.order == 3 and args.workload == "density" and PREDICTOR_N3_DRAM_BYTES_PER_CELL:
         out["roofline"]["traffic"] = PREDICTOR_N3_DRAM_BYTES_PER_CELL * pm.n_cells
-        out["roofline"]["traffic_note"] = ("ncu dram__bytes_read+write of a 12^3 launch scaled by cells "
-                                           "(profiles/step_kernels_density_wave_12c_N3.md)")
+        out["roofline"]["traffic_note"] = "ncu dram__bytes_read+write of a 12^3 launch, scaled by cells"
     out["config"]["cfl"] = cfl
     if rst is not None:
         v_st, ms_st = throughput(red, 5 * rst["n_nodes"], K, rst["ms"])
@@ -477,6 +528,18 @@ def ours(args):
                              "stage_ms_per_step": dict(zip(["limiter_dt", "predictor", "face", "corrector"],
                                                            r64["stage_ms"]))}
         out["fp32_over_fp64"] = value / out["fp64_plain"]["value"]
+        if r32.get("l2") and r64.get("l2") and r32["l2"]["steps"] == r64["l2"]["steps"]:
+            a, b = r32["l2"], r64["l2"]
+            out["fp32_over_fp64_accuracy"] = {
+                "steps": a["steps"], "cfl": cfl, "t_fp32": a["t"], "t_fp64": b["t"],
+                "l2_rho_fp32": a["l2_rho"], "l2_rho_fp64": b["l2_rho"],
+                "rel_l2_fp32_vs_fp64": float(np.linalg.norm(a["rho"] - b["rho"]) / np.linalg.norm(b["rho"])),
+                "note": "both forms after the same CFL steps from the same state, L2 error of rho against the "
+                        "exact density wave (volume-weighted nodal norm); CFL below the paper's 0.3, at which "
+                        "these meshes diverge for N >= 2"}
+    for r in (r32, r64, rst):
+        if r is not None:
+            r.pop("l2", None)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             n_s, rec = oracle_sample(args.order, 1, cfl)

@@ -189,6 +189,36 @@ afe_status afe_get_diagnostics(const afe_mesh* m, double* qbar, int32_t* iterati
 afe_status afe_set_profiling(afe_mesh* m, int on);
 afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset);
 
+/* How the handle's step runs (a host-side report; no GPU work).  The FP32 form keeps each
+ * cell's fixed-point iteration in the shared memory of one predictor block when the cell fits
+ * (fp32_shared = 1): the right-hand side of Eq. ader4 is formed in chunks of sub-tets (16 per
+ * chunk at N = 2, 3 when the cell leaves room for them, else 8: a "narrow" cell) and M_i^-1
+ * streams through a ring of 32-row stages (as many as fit, at most 8; a cell whose N_i is
+ * not a multiple of 32 ends with a partial, "masked" stage).  Meshes whose largest cell
+ * does not fit that plan run the FP32 form with global-memory scratch on the CUDA cores
+ * (fp32_shared = 0), as does, always, the FP64 form. */
+typedef struct {
+  int32_t fp32_shared;     /* 1: FP32 shared-memory predictor (M_i^-1 apply on the tensor cores)  */
+  int32_t corrector_block; /* 1: FP32 corrector with one block per cell                           */
+  int64_t smem_bytes;      /* dynamic shared memory of one predictor block (0 when not used)     */
+  int32_t max_nodes;       /* largest N_i                                                          */
+  int32_t max_subtets;     /* most sub-tets in one cell                                            */
+  int32_t ring_min;        /* fewest M_i^-1 stages in the ring over the cells (the largest cell)   */
+  int32_t ring_max;        /* most stages over the cells                                           */
+  int64_t narrow_cells;    /* cells whose right-hand side takes the narrow chunks                  */
+  int64_t masked_cells;    /* cells whose last M_i^-1 stage is partial                             */
+} afe_plan;
+afe_status afe_plan_info(const afe_mesh* m, afe_plan* out);
+
+/* Poll limit of the first bounded wait the FP32 shared-memory predictor makes for every cell
+ * (for the cell's sub-tet records to arrive in shared memory; default 1048576 polls, far
+ * beyond the time the copy takes).  A wait that runs out makes the block wait, with the
+ * default limit, for the copy it issued, leave the kernel, and the step report
+ * AFE_ETIMEOUT; the state of the handle is then undefined.  polls = 0 gives up at once:
+ * it exists to exercise that failure path.  Batches copy the setting when created.
+ * polls < 0 returns AFE_EINVAL. */
+afe_status afe_set_wait_limit(afe_mesh* m, int32_t polls);
+
 /* Conserved totals of a caller-provided device state, with no device memory allocated by the
  * call.  The paper has no counterpart: this serves callers that must not call cudaMalloc at
  * the point of use, e.g. code running inside a framework whose caching allocator owns all
@@ -202,7 +232,8 @@ afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset);
  * partials of AFE_NOALLOC_CHUNK nodes each, 160 KiB, held by every GPU that loads the library
  * until the process exits), so meshes with more than AFE_NOALLOC_MAX_NODES nodes are rejected
  * with AFE_EINVAL.  The first call on a device looks up that array's device address; make
- * that first call before any stream capture.  All calls share the one array: calls that
+ * that first call before any stream capture (a first call on a capturing stream returns
+ * AFE_EINVAL and does nothing).  All calls share the one array: calls that
  * overlap on the GPU (different streams, no ordering between them) race and must not be
  * issued.  Nothing in the array needs to start at zero: each call writes every partial it
  * reads. */

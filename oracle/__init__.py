@@ -13,7 +13,6 @@ Modules
 ``mesh``     per-cell AFE nodes, Jacobians, mass matrices, faces (Sec. 4.1, 4.3, 4.4)
 ``scheme``   time step, limiter, predictor, Rusanov fluxes, corrector (Sec. 4.2-4.5)
 ``density_wave_run``  command-line full-length run of the density-wave accuracy case
-``local_amplification``  command-line analysis: one cell's linearised one-step map
 
 Parity pinning: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute-force quadrature, invariants or values printed in

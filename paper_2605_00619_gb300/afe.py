@@ -59,6 +59,20 @@ class afe_stats(ctypes.Structure):
     ]
 
 
+class afe_plan(ctypes.Structure):
+    _fields_ = [
+        ("fp32_shared", ctypes.c_int32),
+        ("corrector_block", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int64),
+        ("max_nodes", ctypes.c_int32),
+        ("max_subtets", ctypes.c_int32),
+        ("ring_min", ctypes.c_int32),
+        ("ring_max", ctypes.c_int32),
+        ("narrow_cells", ctypes.c_int64),
+        ("masked_cells", ctypes.c_int64),
+    ]
+
+
 class AfeError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {message}")
@@ -95,6 +109,8 @@ _SIGS = {
     "afe_device_bytes": (ctypes.c_int, [_P, _I64]),
     "afe_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "afe_conserved_totals_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
+    "afe_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(afe_plan)]),
+    "afe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32]),
     "afe_stage_times": (ctypes.c_int, [_P, _D, _I64, ctypes.c_int]),
     "afe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "afe_batch_step_async": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
@@ -285,6 +301,16 @@ def afe_stage_times(m, reset: bool = True):
     n = ctypes.c_int64()
     _check(lib().afe_stage_times(m, _dptr(ms), ctypes.byref(n), int(bool(reset))))
     return ms, int(n.value)
+
+
+def afe_plan_info(m) -> afe_plan:
+    out = afe_plan()
+    _check(lib().afe_plan_info(m, ctypes.byref(out)))
+    return out
+
+
+def afe_set_wait_limit(m, polls: int):
+    _check(lib().afe_set_wait_limit(m, int(polls)))
 
 
 AFE_NOALLOC_CHUNK = 65536

@@ -395,6 +395,7 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
   d.picard_max = p->picard_max;
   d.limiter = p->limiter;
   d.eq = p->equations;
+  d.first_wait_polls = afe::kWaitPolls;
   afe_mesh* M = m.get();
   AFE_TRY(M->upload((int64_t**)&d.node_ptr, T.node_ptr));
   AFE_TRY(M->upload((int64_t**)&d.sub_ptr, T.sub_ptr));
@@ -722,6 +723,41 @@ afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset) 
   return AFE_OK;
 }
 
+afe_status afe_plan_info(const afe_mesh* m, afe_plan* out) {
+  if (!m || !out) return fail(AFE_EINVAL, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  const afe::Topology& T = m->topo;
+  const int N = m->p.order;
+  const bool fp32 = m->p.precision == AFE_FP32;
+  out->max_nodes = T.Nmax;
+  out->max_subtets = T.Smax;
+  out->fp32_shared = (fp32 && m->f32_ok) ? 1 : 0;
+  out->corrector_block = (fp32 && corrector_f32_fits(T.Nmax)) ? 1 : 0;
+  if (!out->fp32_shared) return AFE_OK;
+  out->smem_bytes = (int64_t)m->f32_smem;
+  int rmin = afe::kF32MaxStages, rmax = 0;
+  for (int64_t c = 0; c < T.C; ++c) {
+    const int Ni = (int)(T.node_ptr[c + 1] - T.node_ptr[c]);
+    const afe::F32CellPlan P = afe::f32_cell_plan(N, m->f32_smem, T.Smax, Ni);
+    rmin = std::min(rmin, P.nstage);
+    rmax = std::max(rmax, P.nstage);
+    if (afe::f32_ntp(N) == 4 && !P.wide) out->narrow_cells += 1;
+    if (Ni % afe::kF32Rows) out->masked_cells += 1;
+  }
+  out->ring_min = rmin;
+  out->ring_max = rmax;
+  return AFE_OK;
+}
+
+afe_status afe_set_wait_limit(afe_mesh* m, int32_t polls) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  if (polls < 0) return fail(AFE_EINVAL, "polls must be >= 0");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  m->dm.first_wait_polls = polls;
+  sync_self(m);
+  return AFE_OK;
+}
+
 afe_status afe_device_bytes(const afe_mesh* m, int64_t* bytes) {
   if (!m || !bytes) return fail(AFE_EINVAL, "NULL argument");
   *bytes = m->bytes;
@@ -981,7 +1017,7 @@ __global__ void noalloc_final_kernel(const double* partials, int np, double* out
 extern "C" afe_status afe_conserved_totals_noalloc(const afe_mesh* m, const double* dq, double* dtotals,
                                                    void* cuda_stream) {
   if (!m || !dq || !dtotals) return fail(AFE_EINVAL, "NULL argument");
-  const int64_t n = m->topo.n_nodes;
+  const int64_t n = m->topo.n_nodes;  // >= 1 for every handle afe_mesh_create returns
   if (n > AFE_NOALLOC_MAX_NODES)
     return fail(AFE_EINVAL, "afe_conserved_totals_noalloc: " + std::to_string(n) +
                                 " nodes exceed the fixed scratch limit of " + std::to_string(AFE_NOALLOC_MAX_NODES) +
@@ -991,12 +1027,21 @@ extern "C" afe_status afe_conserved_totals_noalloc(const afe_mesh* m, const doub
   int prev = -1;
   AFE_CUDA(cudaGetDevice(&prev));
   if (prev != m->device) AFE_CUDA(cudaSetDevice(m->device));
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : m->stream;
   double* scratch = nullptr;
   {
     // one-time set-up per device, with that device current: the host-side symbol is only a
     // stand-in, the kernels need the array's device address
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_ptr[m->device]) {
+      // the look-up must not happen inside a stream capture: refuse with a clear message
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      const cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+      if (ce != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        if (prev != m->device) cudaSetDevice(prev);
+        return fail(AFE_EINVAL, "afe_conserved_totals_noalloc: the first call on a device must come before any "
+                                "stream capture (it looks up the scratch array's device address)");
+      }
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
       if (e != cudaSuccess) {
@@ -1007,10 +1052,9 @@ extern "C" afe_status afe_conserved_totals_noalloc(const afe_mesh* m, const doub
     }
     scratch = g_noalloc_ptr[m->device];
   }
-  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : m->stream;
   const int np = (int)((n + AFE_NOALLOC_CHUNK - 1) / AFE_NOALLOC_CHUNK);
-  noalloc_partial_kernel<<<np, 256, 0, st>>>(m->dm.wvec, dq, n, scratch);
-  noalloc_final_kernel<<<1, 32, 0, st>>>(scratch, np, dtotals);
+  if (np > 0) noalloc_partial_kernel<<<np, 256, 0, st>>>(m->dm.wvec, dq, n, scratch);
+  noalloc_final_kernel<<<1, 32, 0, st>>>(scratch, np, dtotals);  // np = 0 writes zeros
   cudaError_t e = cudaGetLastError();
   if (prev != m->device) cudaSetDevice(prev);
   if (e != cudaSuccess) return fail(AFE_ECUDA, std::string("afe_conserved_totals_noalloc launch: ") + cudaGetErrorString(e));

@@ -73,6 +73,7 @@ struct DevMesh {
   // physics
   double gamma, Rgas, cv, cfl, m1, mu0, Pr, kappa0, tol, h_min;
   int picard_max, limiter, eq;
+  int first_wait_polls;  // poll limit of the FP32 predictor's first bounded wait per cell
 };
 
 // A set of meshes stepped by one launch per stage (one mesh is a batch of one).  The whole

@@ -73,9 +73,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: false if it did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < (1 << 20); ++i)
+// Bounded wait on an mbarrier phase: false if it did not complete within `polls` polls.
+constexpr int kWaitPolls = 1 << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int polls = kWaitPolls) {
+  for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -185,6 +186,26 @@ __host__ __device__ constexpr size_t f32_sB_bytes(int N) { return f32_sB_bytes(N
 __host__ __device__ constexpr size_t f32_inc_bytes(int N, int Smax) {
   return f32_up128((size_t)Smax * np_of(N) * 4) + f32_up128((size_t)(kF32MaxNodes + 1) * 4);
 }
+// Per-cell plan of the predictor's shared memory: whether the right-hand side takes chunks
+// of 2 CH sub-tets (4-time contraction tiles) and how many M_i^-1 stages the ring holds.
+// The kernel and the host-side plan report use this one function.
+struct F32CellPlan {
+  bool wide;
+  int nstage;
+};
+__host__ __device__ inline F32CellPlan f32_cell_plan(int N, size_t smem_bytes, int Smax, int Ni) {
+  const int SR = f32_row_stride(N), SRN = f32_rhs_stride(N), CH = f32_chunk(N);
+  const size_t fixed = f32_up128((size_t)Smax * f32_rec_bytes(N)) + f32_inc_bytes(N, Smax) +
+                       f32_up128((size_t)Ni * SR * 4) + f32_up128((size_t)Ni * SRN * 4);
+  const size_t region = smem_bytes > fixed ? smem_bytes - fixed : 0;
+  F32CellPlan P;
+  P.wide = f32_ntp(N) == 4 && region >= f32_sR_bytes(N, 2 * CH) + f32_sB_bytes(N, 2 * CH);
+  const size_t stage = (size_t)kF32Rows * minv_ld(Ni) * 4;
+  const size_t ns = region / stage;
+  P.nstage = (int)(ns < (size_t)kF32MaxStages ? ns : (size_t)kF32MaxStages);
+  return P;
+}
+
 inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
   const size_t phase1 = f32_sR_bytes(N) + f32_sB_bytes(N);
   const size_t stage = (size_t)kF32Rows * minv_ld(Nmax) * 4;
@@ -297,6 +318,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   __syncthreads();
   uint32_t phase = 0;
   uint32_t fpar = 0, epar = 0;  // parities of the next completion of sfull[s] / sempty[s]
+  // producer lane: parity of the phase of sfull[s] its next copy into slot s completes, and
+  // the slots that have received a copy (to drain exactly the copies issued)
+  uint32_t ipar = 0, issued = 0;
   const int64_t total = bt.cpre[bt.nh];
   auto rec_g = [&](int k) { return reinterpret_cast<const float*>(srec + (size_t)k * REC); };
   auto rec_a = [&](int k) { return reinterpret_cast<const uint16_t*>(srec + (size_t)k * REC + 40); };
@@ -325,17 +349,16 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     float* sq = reinterpret_cast<float*>(cell_base);
     float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
     unsigned char* const shared_region = cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4);
-    // chunks of 2 CH sub-tets (4-time contraction tiles) when the cell leaves room for them
-    const size_t region_bytes = (size_t)smem_bytes - (size_t)(shared_region - smem_raw);
-    const bool wide = NTP == 4 && region_bytes >= f32_sR_bytes(N, 2 * CH) + f32_sB_bytes(N, 2 * CH);
+    // chunks of 2 CH sub-tets (4-time contraction tiles) when the cell leaves room for them;
+    // the M_i^-1 ring takes as many stages as fit (the same plan the host reports)
+    const F32CellPlan plan = f32_cell_plan(N, (size_t)smem_bytes, bt.Smax, Ni);
+    const bool wide = plan.wide;
     const int CHc = wide ? 2 * CH : CH;
     float* sR = reinterpret_cast<float*>(shared_region);                          // phase 1, epilogue
     float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc][3 NP][5][NTP]
     float* ring = reinterpret_cast<float*>(shared_region);                  // phase 2
     const int stage_floats = kF32Rows * LD;
-    const int nstage = min(kF32MaxStages,
-                           (int)(((size_t)smem_bytes - (size_t)(reinterpret_cast<unsigned char*>(ring) - smem_raw)) /
-                                 ((size_t)stage_floats * 4)));
+    const int nstage = plan.nstage;
     const int nblk = (Ni + kF32Rows - 1) / kF32Rows;
 
     // the cell's sub-tet records arrive by one bulk copy while the state is loaded
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       for (int e = tid; e < ninc; e += kF32Threads) sinc[e] = m.inc[ib + e];
       for (int e = tid; e <= Ni; e += kF32Threads) sincp[e] = (int)(m.inc_ptr[n0 + e] - ib);
     }
-    if (tid == 0 && !mbar_wait_bounded(&sbar, phase & 1u)) {
+    if (tid == 0 && !mbar_wait_bounded(&sbar, phase & 1u, m.first_wait_polls)) {
       atomicOr(&m.flags[F_TIMEOUT], 1);
       sAbort = 1;
     }
@@ -520,6 +543,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
             bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
                      &sfull[s]);
+            issued |= 1u << s;
+            ipar ^= 1u << s;
           }
           // every stage released by the consumers before the ring is reused
           for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
@@ -596,10 +621,11 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       }
       __syncthreads();  // every thread has finished reading RHS and the ring is drained
       if (sAbort) {
-        // a bounded wait ran out (flags[F_TIMEOUT] is set): wait (bounded) for copies still
-        // in flight into the ring, then leave
+        // a bounded wait ran out (flags[F_TIMEOUT] is set): wait (bounded) for the last copy
+        // issued into every slot (the phase its completion ends), then leave
         if (!consumer && lane == 0)
-          for (int s2 = 0; s2 < nstage; ++s2) (void)mbar_wait_bounded(&sfull[s2], (fpar >> s2) & 1u);
+          for (int s2 = 0; s2 < kF32MaxStages; ++s2)
+            if ((issued >> s2) & 1u) (void)mbar_wait_bounded(&sfull[s2], ((ipar >> s2) & 1u) ^ 1u);
         __syncthreads();
         return;
       }

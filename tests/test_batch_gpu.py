@@ -171,3 +171,63 @@ def test_graph_recaptured_when_dt_changes(afe, meshes):
         np.testing.assert_array_equal(afe.afe_get_state(h), q)
     for h, _ in allm:
         afe.afe_mesh_destroy(h)
+
+
+def _oracle_run(afe, pm, p, h, u0, nsteps):
+    """The oracle's result of nsteps CFL steps from u0 (library node order), and the
+    permutation library node -> oracle node."""
+    from oracle import scheme
+    from oracle.mesh import from_polymesh
+    from tests.harness import node_permutation, oracle_params
+    om = from_polymesh(pm, p.order)
+    perm = node_permutation(om, afe.afe_get_node_coords(h), afe.afe_node_ptr(h, pm.n_cells))
+    u = np.empty_like(u0)
+    u[perm] = u0
+    prm = oracle_params(p)
+    uc = om.split(u)
+    for _ in range(nsteps):
+        uc, _ = scheme.step(om, uc, prm)
+    return np.concatenate(uc)[perm]
+
+
+def test_every_batch_member_matches_the_oracle(afe, meshes):
+    """Each member of the mixed batch (density wave, limited explosion on a box,
+    Navier-Stokes, a state at rest), stepped 3 CFL steps inside the batch with the captured
+    graph, against the FP64 oracle: relative L2 <= 1e-5 per conserved variable."""
+    from tests.harness import rel_l2
+    mem = _members(afe, meshes)
+    keys = ["a", "b", "c", "a"]
+    got, statuses, _ = _batched(afe, mem, [1, 2], True)
+    for i, ((h, u0), key, (q, _)) in enumerate(zip(mem, keys, got)):
+        assert statuses[i] in (0, 5)
+        p = afe.afe_default_params(2, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+        if i == 1:
+            p.limiter = 1
+        if i == 2:
+            p.equations, p.mu, p.kappa, p.Pr = afe.AFE_NAVIER_STOKES, 0.005, -1.0, 0.71
+        ref = _oracle_run(afe, meshes[key], p, h, u0, 3)
+        assert rel_l2(q, ref) <= 1e-5, f"member {i}"
+    for h, _ in mem:
+        afe.afe_mesh_destroy(h)
+
+
+def test_served_requests_match_the_oracle(afe, meshes):
+    """Requests run through the continuous-batching server (their batch changes as others
+    arrive and retire) end within the reduced-precision tolerance of the FP64 oracle run of
+    the same request alone."""
+    from paper_2605_00619_gb300.serving import GpuEngine, Request, Server
+    from tests.harness import rel_l2
+    p = afe.afe_default_params(2, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+    cat = {"a": meshes["a"]}
+    eng = GpuEngine(cat, {"a": 2}, p)
+    for s in eng.slots:
+        eng.default_state.setdefault(s.mesh, states.density_wave(afe.afe_get_node_coords(s.handle)))
+    reqs = [Request(i, "a", n, 0.0, q0=eng.default_state["a"] * (1.0 + 0.02 * i)) for i, n in enumerate((3, 2, 4))]
+    stats = Server(eng, max_chunk=2, keep_results=True).run(reqs)
+    assert stats.requests == 3 and stats.failed == 0
+    h = afe.create_from_polymesh(meshes["a"], p)
+    for r in reqs:
+        ref = _oracle_run(afe, meshes["a"], p, h, r.q0, r.nsteps)
+        assert rel_l2(r.q, ref) <= 1e-5, f"request {r.rid}"
+    afe.afe_mesh_destroy(h)
+    eng.close()

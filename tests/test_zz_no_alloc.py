@@ -41,3 +41,53 @@ def test_noalloc_totals_match_afe_get_stats_on_two_calls():
             np.testing.assert_allclose(out.cpu().numpy(), expected, rtol=1e-13, atol=0)
     finally:
         afe.afe_mesh_destroy(h)
+
+
+_FIRST_CALL_IN_CAPTURE = r"""
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np
+import torch
+from inputs import states
+from inputs.voronoi import periodic_voronoi
+from paper_2605_00619_gb300 import afe
+pm = periodic_voronoi(2)
+h = afe.create_from_polymesh(pm, afe.afe_default_params(1))
+u = states.density_wave(afe.afe_get_node_coords(h))
+afe.afe_set_state(h, u)
+dq = torch.from_numpy(u).to("cuda")
+out = torch.zeros(5, dtype=torch.float64, device="cuda")
+s = torch.cuda.Stream()
+g = torch.cuda.CUDAGraph()
+with torch.cuda.graph(g, stream=s):
+    out.add_(1.0)
+    st = afe.afe_conserved_totals_noalloc(h, dq.data_ptr(), out.data_ptr(), s.cuda_stream, check=False)
+    msg = afe.afe_last_error()
+torch.cuda.synchronize()
+st2 = afe.afe_conserved_totals_noalloc(h, dq.data_ptr(), out.data_ptr(), 0, check=False)
+torch.cuda.synchronize()
+ok = np.allclose(out.cpu().numpy(), np.array(afe.afe_get_stats(h).totals), rtol=1e-13, atol=0)
+afe.afe_mesh_destroy(h)
+print("RESULT", st, st2, int(ok), "capture" in msg)
+"""
+
+
+def test_first_call_inside_a_stream_capture_is_refused():
+    """In a fresh process, the first call on the device made while a stream is being captured
+    returns AFE_EINVAL without touching the device (it would have to look up the scratch
+    array's address inside the capture); the next call, after the capture, works."""
+    import os
+    import subprocess
+    import sys
+
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL_IN_CAPTURE.format(root=root)], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT")][-1].split()
+    from paper_2605_00619_gb300 import afe
+    assert int(line[1]) == afe.AFE_EINVAL and line[4] == "True"
+    assert int(line[2]) == afe.AFE_OK and line[3] == "1"
