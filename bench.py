@@ -40,14 +40,12 @@ METRIC = "DOF-updates/s per ADER-DG step"
 # N = 3 within 8 steps at 0.3 and after ~30 at 0.2.
 STABLE_CFL = {1: 0.3, 2: 0.2, 3: 0.15}
 PAPER_CFL = 0.3
-# CFL steps after which both forms' accuracy is compared in the throughput run
-L2_STEPS = 3
 
 # DRAM bytes (read + write) of one predictor_f32_kernel<3> launch per cell of the density-wave
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 12^3 launch
 # of the current kernel; None until that capture exists.  The fixed-point iterations re-read
 # M_i^-1 from L2, so the traffic grows with the cells, not with the iterations.
-PREDICTOR_N3_DRAM_BYTES_PER_CELL = None
+PREDICTOR_N3_DRAM_BYTES_PER_CELL = (807072000 + 40923392) / 1728
 UNIT = "DOF-updates/s"
 
 
@@ -339,6 +337,50 @@ def throughput(red, dofs_per_step, steps, ms):
     return red.sum(dofs_per_step * steps) / (ms_max / 1e3), ms_max
 
 
+def equal_steps_accuracy(N, cfl, n=8, t_end=0.1):
+    """Both forms on the density wave of the throughput workload's order and CFL, on the
+    n^3 mesh of the same generator, to t_end with the same steps: the L2 error of rho against
+    the exact solution (volume-weighted nodal norm) of each form and their relative
+    difference.  The ratio of the throughput line compares the forms at equal steps, so it
+    holds at equal error when these two errors agree."""
+    import numpy as np
+
+    from inputs import states
+    from inputs.voronoi import periodic_voronoi
+    from paper_2605_00619_gb300 import afe
+    pm = periodic_voronoi(n)
+    sub = pm.subtet_coords()
+    vol = np.bincount(np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr)),
+                      weights=np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0, minlength=pm.n_cells)
+    out = {"mesh": f"{n}^3", "N": N, "cfl": cfl, "t": t_end}
+    rho = {}
+    for name, prec in (("fp32", afe.AFE_FP32), ("fp64", afe.AFE_FP64)):
+        fp32 = prec == afe.AFE_FP32
+        p = afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
+                                   picard_max=128 if fp32 else 64, cfl=cfl)
+        h = afe.create_from_polymesh(pm, p)
+        x = afe.afe_get_node_coords(h)
+        ptr = afe.afe_node_ptr(h, pm.n_cells)
+        afe.afe_set_state(h, states.density_wave(x))
+        if name == "fp32":
+            nsteps = int(math.ceil(t_end / afe.afe_compute_dt(h) - 1e-9))
+            dt = t_end / nsteps
+        afe.afe_step_async(h, dt, nsteps)
+        st = afe.afe_sync(h, check=False)
+        q = afe.afe_get_state(h)
+        afe.afe_mesh_destroy(h)
+        e2 = (q[:, 0] - states.density_wave(x, t=t_end)[:, 0]) ** 2
+        out[f"l2_rho_{name}"] = float(np.sqrt(np.sum(vol * np.add.reduceat(e2, ptr[:-1]) / np.diff(ptr))))
+        out[f"status_{name}"] = int(st)
+        rho[name] = q[:, 0]
+    out["steps"] = nsteps
+    out["rel_l2_fp32_vs_fp64"] = float(np.linalg.norm(rho["fp32"] - rho["fp64"]) / np.linalg.norm(rho["fp64"]))
+    out["note"] = ("the throughput ratio is at equal steps; on this smaller mesh of the same generator both forms "
+                   "reach the same L2 error of rho against the exact solution (CFL below the paper's 0.3, at "
+                   "which these meshes diverge for N >= 2)")
+    return out
+
+
 def ours(args):
     import numpy as np
     import torch
@@ -374,10 +416,6 @@ def ours(args):
         pm = periodic_voronoi(args.n, seed=rank)
     stream = torch.cuda.Stream()
     sid = stream.cuda_stream
-    sub = pm.subtet_coords()
-    cell_vol = np.bincount(np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr)),
-                           weights=np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0, minlength=pm.n_cells)
-    del sub
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -407,24 +445,7 @@ def ours(args):
         else:
             u0 = states.density_wave(x)
         afe.afe_set_state(h, u0)
-        # accuracy at equal steps: the density wave after L2_STEPS CFL steps against the exact
-        # solution, taken inside the warm-up (FP32 form) or after the timed steps (FP64 form)
-        l2_rec = None
-
-        def density_l2():
-            st_ = afe.afe_get_stats(h)
-            q_ = afe.afe_get_state(h)
-            e2 = (q_[:, 0] - states.density_wave(x, t=st_.t)[:, 0]) ** 2
-            per_cell = np.add.reduceat(e2, node_ptr[:-1]) / np.diff(node_ptr)
-            return {"steps": int(st_.steps), "t": st_.t, "l2_rho": float(np.sqrt(np.sum(cell_vol * per_cell))),
-                    "rho": q_[:, 0].copy()}
-
-        pre = L2_STEPS if (args.workload == "density" and warmup >= L2_STEPS) else 0
-        if pre:
-            afe.afe_step_async(h, 0.0, pre)
-            afe.afe_sync(h, check=False)
-            l2_rec = density_l2()
-        afe.afe_step_async(h, 0.0, warmup - pre)
+        afe.afe_step_async(h, 0.0, warmup)
         st = afe.afe_sync(h, check=False)
         barrier()
         afe.afe_set_profiling(h, True)
@@ -449,12 +470,10 @@ def ours(args):
         afe.afe_set_profiling(h, False)
         stats = afe.afe_get_stats(h)
         launches = stats.kernel_launches - launches0
-        if l2_rec is None and args.workload == "density" and stats.steps == L2_STEPS:
-            l2_rec = density_l2()
         _, iters, _, _ = afe.afe_get_diagnostics(h, pm.n_cells, qbar=False)
         rec = dict(status=[st, st2], ms=ms, wall=wall, stage_ms=(stage_ms / max(nst, 1)).tolist(), clocks=clk,
                    n_nodes=n_nodes, launches=launches, iters_mean=float(iters.mean()), iters_max=int(iters.max()),
-                   nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h), l2=l2_rec)
+                   nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h))
         rec["f_con"], rec["f_pw"], rec["abytes"], rec["abytes_streamed"] = predictor_model(
             node_ptr, pm.cell_subtet_ptr, iters, args.order, 4 if prec == afe.AFE_FP32 else 8)
         if e2e:
@@ -528,18 +547,8 @@ def ours(args):
                              "stage_ms_per_step": dict(zip(["limiter_dt", "predictor", "face", "corrector"],
                                                            r64["stage_ms"]))}
         out["fp32_over_fp64"] = value / out["fp64_plain"]["value"]
-        if r32.get("l2") and r64.get("l2") and r32["l2"]["steps"] == r64["l2"]["steps"]:
-            a, b = r32["l2"], r64["l2"]
-            out["fp32_over_fp64_accuracy"] = {
-                "steps": a["steps"], "cfl": cfl, "t_fp32": a["t"], "t_fp64": b["t"],
-                "l2_rho_fp32": a["l2_rho"], "l2_rho_fp64": b["l2_rho"],
-                "rel_l2_fp32_vs_fp64": float(np.linalg.norm(a["rho"] - b["rho"]) / np.linalg.norm(b["rho"])),
-                "note": "both forms after the same CFL steps from the same state, L2 error of rho against the "
-                        "exact density wave (volume-weighted nodal norm); CFL below the paper's 0.3, at which "
-                        "these meshes diverge for N >= 2"}
-    for r in (r32, r64, rst):
-        if r is not None:
-            r.pop("l2", None)
+        if args.workload == "density":
+            out["fp32_over_fp64_accuracy"] = equal_steps_accuracy(args.order, cfl)
     if rank == 0 and not args.no_cpu_baseline:
         try:
             n_s, rec = oracle_sample(args.order, 1, cfl)

@@ -4,7 +4,8 @@ large enough for the predictor's narrow chunks and one-stage M_i^-1 ring, cells 
 for the shared-memory plan (the global-scratch kernel), and the bounded-wait failure path.
 
 Bar: relative L2 <= 1e-5 per conserved variable after the stated steps (the reduced-
-precision tolerance); the path each case takes is asserted from afe_plan_info.
+precision tolerance), with the momentum compared as one vector field where a component
+vanishes initially; the path each case takes is asserted from afe_plan_info.
 """
 import math
 
@@ -14,7 +15,7 @@ import pytest
 from inputs import states
 from inputs.lattice import split_cube_lattice
 from inputs.voronoi import box_voronoi, periodic_voronoi
-from tests.harness import Pair, rel_l2
+from tests.harness import Pair, rel_l2, rel_l2_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -54,17 +55,20 @@ def test_fp32_navier_stokes_against_the_oracle(afe):
     assert afe.afe_plan_info(pr.h).fp32_shared == 1
     pr.set_state(states.taylor_green_3d(2 * math.pi * pr.om.node_coords(), p0=10.0))
     _steps(pr, 3)
-    assert rel_l2(pr.lib_state(), pr.u) <= FP32_TOL
+    # w vanishes at t = 0: the momentum is compared as one vector field
+    assert rel_l2_fields(pr.lib_state(), pr.u) <= FP32_TOL
     pr.close()
 
 
 def test_fp32_limiter_against_the_oracle(afe):
-    """Smoothed explosion on a box mesh with the limiter: beta_i > 0 in troubled cells, whose
-    artificial viscosity mu_i > 0 runs the FP32 viscous flux of an Euler problem."""
+    """Converging flow v = -(x - x0) on a box mesh with the limiter: the detector flags the
+    compressed cells (beta_i > 0), whose artificial viscosity mu_i > 0 runs the FP32 viscous
+    flux inside an Euler problem."""
     pm = box_voronoi(3)
     p = _fp32(afe, 2, limiter=1, visc_dt_subtet=1)
     pr = Pair(pm, p)
-    pr.set_state(states.spherical_riemann(pr.om.node_coords(), alpha0=1.5 * pr.om.h_min))
+    x = pr.om.node_coords()
+    pr.set_state(states.primitive_to_conserved(1.0 + 0.1 * np.sin(x.sum(axis=1)), -(x - x.mean(axis=0)), 1.0))
     infos = _steps(pr, 3, allowed=(0, 5))
     assert max(info.beta.max() for info in infos) > 0.0
     _, _, beta, mu = afe.afe_get_diagnostics(pr.h, pm.n_cells, qbar=False)
