@@ -193,8 +193,9 @@ afe_status afe_stage_times(afe_mesh* m, double* ms, int64_t* nsteps, int reset);
  * cell's fixed-point iteration in the shared memory of one predictor block when the cell fits
  * (fp32_shared = 1): the right-hand side of Eq. ader4 is formed in chunks of sub-tets (16 per
  * chunk at N = 2, 3 when the cell leaves room for them, else 8: a "narrow" cell) and M_i^-1
- * streams through a ring of 32-row stages (as many as fit, at most 8; a cell whose N_i is
- * not a multiple of 32 ends with a partial, "masked" stage).  Meshes whose largest cell
+ * streams through a ring of stages of 32 rows (in the tensor-memory form 16 or 8 rows when a
+ * large cell leaves less room; as many stages as fit, at most 8; a cell whose N_i is not a
+ * multiple of the stage height ends with a partial, "masked" stage).  Meshes whose largest cell
  * does not fit that plan run the FP32 form with global-memory scratch on the CUDA cores
  * (fp32_shared = 0), as does, always, the FP64 form. */
 typedef struct {
@@ -207,8 +208,18 @@ typedef struct {
   int32_t ring_max;        /* most stages over the cells                                           */
   int64_t narrow_cells;    /* cells whose right-hand side takes the narrow chunks                  */
   int64_t masked_cells;    /* cells whose last M_i^-1 stage is partial                             */
+  int32_t tcgen05;         /* 1: the M_i^-1 apply runs on the 5th-generation tensor cores with
+                              tensor memory (tcgen05); 0: on the warp-level mma.sync path          */
+  int32_t stage_rows_min;  /* shortest M_i^-1 ring stage over the cells (32, 16 or 8 rows)        */
 } afe_plan;
 afe_status afe_plan_info(const afe_mesh* m, afe_plan* out);
+
+/* Which form of the FP32 predictor's M_i^-1 apply a handle uses: 0 (the default) takes the
+ * tensor-memory form (tcgen05) whenever every cell fits its shared-memory plan (up to 640
+ * nodes per cell), else the mma.sync form; 1 always takes the mma.sync form.  Both compute
+ * the same 3xTF32 product (results agree to FP32 rounding, not bit for bit).  A batch takes
+ * the tensor-memory form unless one of its members asks for 1.  Other values: AFE_EINVAL. */
+afe_status afe_set_predictor_variant(afe_mesh* m, int32_t variant);
 
 /* Poll limit of the first bounded wait the FP32 shared-memory predictor makes for every cell
  * (for the cell's sub-tet records to arrive in shared memory; default 1048576 polls, far

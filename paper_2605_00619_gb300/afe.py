@@ -70,6 +70,8 @@ class afe_plan(ctypes.Structure):
         ("ring_max", ctypes.c_int32),
         ("narrow_cells", ctypes.c_int64),
         ("masked_cells", ctypes.c_int64),
+        ("tcgen05", ctypes.c_int32),
+        ("stage_rows_min", ctypes.c_int32),
     ]
 
 
@@ -111,6 +113,7 @@ _SIGS = {
     "afe_conserved_totals_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "afe_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(afe_plan)]),
     "afe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "afe_set_predictor_variant": (ctypes.c_int, [_P, ctypes.c_int32]),
     "afe_stage_times": (ctypes.c_int, [_P, _D, _I64, ctypes.c_int]),
     "afe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "afe_batch_step_async": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
@@ -307,6 +310,10 @@ def afe_plan_info(m) -> afe_plan:
     out = afe_plan()
     _check(lib().afe_plan_info(m, ctypes.byref(out)))
     return out
+
+
+def afe_set_predictor_variant(m, variant: int):
+    _check(lib().afe_set_predictor_variant(m, int(variant)))
 
 
 def afe_set_wait_limit(m, polls: int):

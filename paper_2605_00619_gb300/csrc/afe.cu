@@ -50,6 +50,9 @@ struct afe_mesh {
   int64_t scratch_stride = 0;
   int pred_grid = 0;
   int f32_ok = 0;        // the shared-memory FP32 predictor is used
+  int f32_tc = 0;        // ... with its M_i^-1 apply on tcgen05 / tensor memory (else mma.sync)
+  int f32_tc_fits = 0;   // every cell fits the tensor-memory plan
+  int variant = 0;       // 0: automatic, 1: mma.sync apply
   size_t f32_smem = 0;
   double* d_totals_partial = nullptr;
   double* d_totals = nullptr;
@@ -104,7 +107,7 @@ struct StepPlan {
   const afe::Batch* b = nullptr;
   cudaStream_t st = nullptr;
   int order = 1, fp32 = 0, limiter = 0, n_sm = 1, diag = 0;
-  int f32_ok = 0;
+  int f32_ok = 0, f32_tc = 0;
   size_t f32_smem = 0;
   const afe::RefData* d_ref = nullptr;
   afe_mesh* single = nullptr;  // nullptr for a batch (FP32 shared-memory kernels only)
@@ -121,6 +124,7 @@ StepPlan plan_of(afe_mesh* m) {
   P.n_sm = m->n_sm;
   P.diag = m->diag;
   P.f32_ok = m->f32_ok;
+  P.f32_tc = m->f32_tc;
   P.f32_smem = m->f32_smem;
   P.d_ref = m->d_ref;
   P.single = m;
@@ -133,8 +137,12 @@ bool corrector_f32_fits(int Nmax) { return Nmax <= 2 * 4 * afe::kCorrThreads; }
 template <int N, typename Real>
 void launch_predictor(const StepPlan& P) {
   if (sizeof(Real) == 4 && P.f32_ok) {
-    afe::predictor_f32_kernel<N><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
-                                                                               (int)P.f32_smem);
+    if (P.f32_tc)
+      afe::predictor_f32_kernel<N, true><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
+                                                                                       (int)P.f32_smem);
+    else
+      afe::predictor_f32_kernel<N, false><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
+                                                                                        (int)P.f32_smem);
     return;
   }
   afe_mesh* m = P.single;
@@ -143,14 +151,19 @@ void launch_predictor(const StepPlan& P) {
 }
 
 // Shared-memory plan of the FP32 predictor; cells too large for it use the global-scratch kernel.
+// The M_i^-1 apply runs on tcgen05 / tensor memory when every cell fits that plan (and the
+// handle does not ask for the mma.sync form), else on mma.sync.
 template <int N>
 afe_status plan_f32(afe_mesh* m) {
-  cudaFuncAttributes fa;
-  AFE_CUDA(cudaFuncGetAttributes(&fa, afe::predictor_f32_kernel<N>));
+  cudaFuncAttributes fa, fb;
+  AFE_CUDA(cudaFuncGetAttributes(&fa, afe::predictor_f32_kernel<N, false>));
+  AFE_CUDA(cudaFuncGetAttributes(&fb, afe::predictor_f32_kernel<N, true>));
   int optin = 0;
   AFE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device));
-  const size_t limit = (size_t)optin - fa.sharedSizeBytes - 1024;
+  const size_t limit = (size_t)optin - std::max(fa.sharedSizeBytes, fb.sharedSizeBytes) - 1024;
   m->f32_ok = 0;
+  m->f32_tc = 0;
+  m->f32_tc_fits = 0;
   if (m->dm.Nmax > afe::predictor_f32_max_nodes(N)) return AFE_OK;
   const size_t need = afe::predictor_f32_smem(N, m->dm.Nmax, m->dm.Smax);
   if (need > limit) return AFE_OK;
@@ -158,7 +171,12 @@ afe_status plan_f32(afe_mesh* m) {
   const size_t b = limit / 128 * 128;
   m->f32_ok = 1;
   m->f32_smem = b;
-  AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+  m->f32_tc_fits = afe::tc_cell_plan(N, b, m->dm.Smax, m->dm.Nmax).ok ? 1 : 0;
+  m->f32_tc = (m->f32_tc_fits && m->variant == 0) ? 1 : 0;
+  AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)b));
+  AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)b));
   return AFE_OK;
 }
 
@@ -735,17 +753,40 @@ afe_status afe_plan_info(const afe_mesh* m, afe_plan* out) {
   out->corrector_block = (fp32 && corrector_f32_fits(T.Nmax)) ? 1 : 0;
   if (!out->fp32_shared) return AFE_OK;
   out->smem_bytes = (int64_t)m->f32_smem;
-  int rmin = afe::kF32MaxStages, rmax = 0;
+  out->tcgen05 = m->f32_tc;
+  int rmin = afe::kF32MaxStages, rmax = 0, hmin = afe::kF32Rows;
   for (int64_t c = 0; c < T.C; ++c) {
     const int Ni = (int)(T.node_ptr[c + 1] - T.node_ptr[c]);
-    const afe::F32CellPlan P = afe::f32_cell_plan(N, m->f32_smem, T.Smax, Ni);
-    rmin = std::min(rmin, P.nstage);
-    rmax = std::max(rmax, P.nstage);
-    if (afe::f32_ntp(N) == 4 && !P.wide) out->narrow_cells += 1;
-    if (Ni % afe::kF32Rows) out->masked_cells += 1;
+    bool wide;
+    int ns, rows;
+    if (m->f32_tc) {
+      const afe::TcCellPlan P = afe::tc_cell_plan(N, m->f32_smem, T.Smax, Ni);
+      wide = P.wide;
+      ns = P.nstage;
+      rows = P.rows;
+    } else {
+      const afe::F32CellPlan P = afe::f32_cell_plan(N, m->f32_smem, T.Smax, Ni);
+      wide = P.wide;
+      ns = P.nstage;
+      rows = afe::kF32Rows;
+    }
+    rmin = std::min(rmin, ns);
+    rmax = std::max(rmax, ns);
+    hmin = std::min(hmin, rows);
+    if (afe::f32_ntp(N) == 4 && !wide) out->narrow_cells += 1;
+    if (Ni % rows) out->masked_cells += 1;
   }
   out->ring_min = rmin;
   out->ring_max = rmax;
+  out->stage_rows_min = hmin;
+  return AFE_OK;
+}
+
+afe_status afe_set_predictor_variant(afe_mesh* m, int32_t variant) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  if (variant != 0 && variant != 1) return fail(AFE_EINVAL, "variant must be 0 (automatic) or 1 (mma.sync)");
+  m->variant = variant;
+  m->f32_tc = (m->f32_ok && m->f32_tc_fits && variant == 0) ? 1 : 0;
   return AFE_OK;
 }
 
@@ -885,6 +926,9 @@ afe_status afe_batch_create(afe_mesh* const* members, int n_members, void* cuda_
   P.diag = 0;
   P.f32_ok = 1;
   P.f32_smem = m0->f32_smem;
+  P.f32_tc = afe::tc_cell_plan(P.order, P.f32_smem, Smax, Nmax).ok ? 1 : 0;
+  for (afe_mesh* m : b->mem)
+    if (m->variant != 0) P.f32_tc = 0;
   P.d_ref = m0->d_ref;
   P.single = nullptr;
   P.prof = nullptr;

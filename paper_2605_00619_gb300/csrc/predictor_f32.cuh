@@ -141,6 +141,67 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// ---- 5th-generation tensor cores (tcgen05) and tensor memory (TMEM).
+// Ordering between thread-synchronising operations and tcgen05 work.
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Whole warp: allocate `cols` columns (a power of two >= 32) of this SM's tensor memory; the
+// address is written to *dst in shared memory.  The block holds it until tmem_dealloc.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+// Shared-memory matrix descriptor of a K-major operand without swizzle: 8-row x 16-byte
+// core matrices, `lbo` bytes between K-adjacent ones, `sbo` bytes between row-adjacent ones.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B (both K-major), M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+// D[128 x N] (+)= A[128 x 8] * B[N x 8]^T, A in tensor memory (lane = row, column = k), B in
+// shared memory.  The tensor core reads each FP32 operand as TF32 by dropping its 13 low
+// mantissa bits (truncation).  Issued by one thread; completion is tracked by tc_commit.
+__device__ __forceinline__ void tc_mma_tmem_a(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Arrive once on `bar` when every tcgen05.mma this thread issued before has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// Warp-wide stores to / loads from tensor memory, shape 32x32b: lane l of the warp writes
+// (reads) lane (quarter * 32 + l) of the addressed rows, consecutive columns.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 16 consecutive columns, waiting for the load in the same statement (the registers are
+// valid only after the wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+// FP32 -> TF32 by truncation (the value the tensor core reads) and the remainder.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
 // Largest cell (nodes) the FP32 predictor handles: up to kF32Items (node, time slice) gather
 // items and two 4-row groups of the M_i^-1 apply per thread.
 constexpr int kF32MaxNodes = 640;
@@ -206,6 +267,63 @@ __host__ __device__ inline F32CellPlan f32_cell_plan(int N, size_t smem_bytes, i
   return P;
 }
 
+// Tensor-memory form of the M_i^-1 apply: per 128-row tile of Y one accumulator in tensor
+// memory, D[128 x 2 NB] = (A_hi + A_lo) [B_hi | B_lo] with A = the tile's rows of M_i^-1
+// (staged into tensor memory, split into the TF32 value and its remainder) and B = the
+// right-hand side split the same way, stored in shared memory as one K-major operand of
+// 2 NB rows (NB = 5 NTP rounded up to 8).  Y = D[:, 0:NB] + D[:, NB:2 NB] (3xTF32 plus the
+// negligible lo * lo product).
+constexpr int tc_nb(int N) { return (5 * f32_ntp(N) + 7) / 8 * 8; }
+constexpr int kTcMaxTiles = 5;      // 128-row tiles: cells of up to 640 nodes
+constexpr int kTcGroups = 3;        // groups of 4 warps that stage M_i^-1 and read Y
+constexpr int kTcStagers = 4 * kTcGroups;
+constexpr int kTcDCols = 48;        // tensor-memory columns per accumulator (2 NB <= 48)
+constexpr int kTcACol0 = kTcMaxTiles * kTcDCols;  // first column of the A staging buffers
+constexpr int kTcCols = 512;
+// Bytes of the right-hand-side operand: 2 NB rows x Kp (N_i rounded up to 16) TF32 words.
+__host__ __device__ inline size_t tc_bop_bytes(int N, int Ni) {
+  const size_t Kp = (size_t)(Ni + 15) / 16 * 16;
+  return (size_t)(2 * tc_nb(N)) * Kp * 4;
+}
+struct TcCellPlan {
+  bool ok;      // the cell fits this form
+  bool wide;    // right-hand side in chunks of 2 CH sub-tets
+  int rows;     // rows of M_i^-1 per ring stage (32, 16 or 8)
+  int slice;    // rows (= K columns) staged into tensor memory at a time: min(16, rows)
+  int nstage;   // stages the ring holds
+  int ntiles;   // 128-row tiles of Y
+};
+__host__ __device__ inline TcCellPlan tc_cell_plan(int N, size_t smem_bytes, int Smax, int Ni) {
+  const int SR = f32_row_stride(N), CH = f32_chunk(N);
+  const size_t fixed = f32_up128((size_t)Smax * f32_rec_bytes(N)) + f32_inc_bytes(N, Smax) +
+                       f32_up128((size_t)Ni * SR * 4);
+  const size_t region = smem_bytes > fixed ? smem_bytes - fixed : 0;
+  TcCellPlan P{};
+  P.wide = f32_ntp(N) == 4 && region >= f32_sR_bytes(N, 2 * CH) + f32_sB_bytes(N, 2 * CH);
+  const bool narrow_ok = region >= f32_sR_bytes(N, CH) + f32_sB_bytes(N, CH);
+  const size_t bop = f32_up128(tc_bop_bytes(N, Ni));
+  const size_t room = region > bop ? region - bop : 0;
+  int best = 0, best_ns = 0;
+  for (int R = 32; R >= 8; R /= 2) {  // the tallest stage of which two fit, else of which one fits
+    const size_t ns = room / ((size_t)R * minv_ld(Ni) * 4);
+    if (ns >= 2) {
+      best = R;
+      best_ns = (int)(ns < (size_t)kF32MaxStages ? ns : (size_t)kF32MaxStages);
+      break;
+    }
+    if (ns == 1 && best == 0) {
+      best = R;
+      best_ns = 1;
+    }
+  }
+  P.rows = best;
+  P.nstage = best_ns;
+  P.slice = best < 16 ? best : 16;
+  P.ntiles = (Ni + 127) / 128;
+  P.ok = narrow_ok && best > 0 && P.ntiles <= kTcMaxTiles && Ni <= kF32MaxNodes;
+  return P;
+}
+
 inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
   const size_t phase1 = f32_sR_bytes(N) + f32_sB_bytes(N);
   const size_t stage = (size_t)kF32Rows * minv_ld(Nmax) * 4;
@@ -256,7 +374,9 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
     for (int v = 0; v < 5; ++v) out[d][v] = scale * (g[d * 3 + 0] * F[0][v] + g[d * 3 + 1] * F[1][v] + g[d * 3 + 2] * F[2][v]);
 }
 
-template <int N>
+// TC = true: the M_i^-1 apply on the 5th-generation tensor cores with tensor memory (tcgen05);
+// TC = false: the same product with mma.sync on the per-warp tensor-core path.
+template <int N, bool TC>
 __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __grid_constant__ Batch bt,
                                                                         const RefData* __restrict__ ref,
                                                                         int diag, int smem_bytes) {
@@ -278,6 +398,13 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   __shared__ int sAbort;
   __shared__ float sred[2][kF32Warps];
   __shared__ int64_t sCell;
+  // tensor-memory form: per (tile, buffer) "A staged" and "MMAs done reading A", per tile
+  // "accumulator complete", per staging group a drain barrier; the tensor-memory address
+  __shared__ __align__(8) uint64_t safull[TC ? 2 * kTcMaxTiles : 1];
+  __shared__ __align__(8) uint64_t saempty[TC ? 2 * kTcMaxTiles : 1];
+  __shared__ __align__(8) uint64_t sdfull[TC ? kTcMaxTiles : 1];
+  __shared__ __align__(8) uint64_t sdrain[TC ? kTcGroups : 1];
+  __shared__ uint32_t stmem;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Nmax = bt.Nmax;
@@ -310,12 +437,32 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     mbar_init(&sbar, 1);
     for (int i = 0; i < kF32MaxStages; ++i) {
       mbar_init(&sfull[i], 1);
-      mbar_init(&sempty[i], kF32Consumers);
+      mbar_init(&sempty[i], TC ? kTcStagers : kF32Consumers);
+    }
+    if constexpr (TC) {
+      for (int i = 0; i < 2 * kTcMaxTiles; ++i) {
+        mbar_init(&safull[i], 4);
+        mbar_init(&saempty[i], 1);
+      }
+      for (int i = 0; i < kTcMaxTiles; ++i) mbar_init(&sdfull[i], 1);
+      for (int i = 0; i < kTcGroups; ++i) mbar_init(&sdrain[i], 1);
     }
     sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if constexpr (TC) {
+    if (warp == 0) tmem_alloc(&stmem, kTcCols);  // one block per SM: all 512 columns
+    tc_fence_before();
+  }
   __syncthreads();
+  if constexpr (TC) tc_fence_after();
+  const uint32_t tmem = TC ? stmem : 0u;
+  // tensor-memory form: parities / counts of the barriers this thread waits on or tracks
+  uint32_t afp = 0;     // issuer: parity of the next completion of safull[i]
+  uint32_t acnt = 0;    // staging group: parity of the commits issued into saempty[i] so far
+  uint32_t aever = 0;   // staging group: saempty[i] has received a commit
+  uint32_t dpar = 0;    // staging group: parity of the next completion of sdfull[T]
+  (void)afp; (void)acnt; (void)aever; (void)dpar; (void)tmem;
   uint32_t phase = 0;
   uint32_t fpar = 0, epar = 0;  // parities of the next completion of sfull[s] / sempty[s]
   // producer lane: parity of the phase of sfull[s] its next copy into slot s completes, and
@@ -347,19 +494,25 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const float* minv = m.minv32 + m.minv_ptr[c];
     const uint32_t* inc = sinc;  // the cell's incidences, staged in shared memory below
     float* sq = reinterpret_cast<float*>(cell_base);
+    // mma.sync form: RHS / Y rows [N_i][SRN] after q; tensor-memory form: none (the
+    // right-hand side operand lives in the shared region, Y in tensor memory)
     float* srhs = reinterpret_cast<float*>(cell_base + up((size_t)Ni * SR * 4));
-    unsigned char* const shared_region = cell_base + up((size_t)Ni * SR * 4) + up((size_t)Ni * SRN * 4);
+    unsigned char* const shared_region = cell_base + up((size_t)Ni * SR * 4) + (TC ? 0 : up((size_t)Ni * SRN * 4));
     // chunks of 2 CH sub-tets (4-time contraction tiles) when the cell leaves room for them;
-    // the M_i^-1 ring takes as many stages as fit (the same plan the host reports)
+    // the M_i^-1 ring takes as many stages as fit (the same plans the host reports)
     const F32CellPlan plan = f32_cell_plan(N, (size_t)smem_bytes, bt.Smax, Ni);
-    const bool wide = plan.wide;
+    const TcCellPlan tplan = tc_cell_plan(N, (size_t)smem_bytes, bt.Smax, Ni);
+    const bool wide = TC ? tplan.wide : plan.wide;
     const int CHc = wide ? 2 * CH : CH;
     float* sR = reinterpret_cast<float*>(shared_region);                          // phase 1, epilogue
     float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc][3 NP][5][NTP]
-    float* ring = reinterpret_cast<float*>(shared_region);                  // phase 2
-    const int stage_floats = kF32Rows * LD;
-    const int nstage = plan.nstage;
-    const int nblk = (Ni + kF32Rows - 1) / kF32Rows;
+    // phase 2: the ring of M_i^-1 stages (after the right-hand-side operand in the TC form)
+    float* bop = reinterpret_cast<float*>(shared_region);
+    float* ring = reinterpret_cast<float*>(shared_region + (TC ? f32_up128(tc_bop_bytes(N, Ni)) : 0));
+    const int srows = TC ? tplan.rows : kF32Rows;  // rows of M_i^-1 per stage
+    const int stage_floats = srows * LD;
+    const int nstage = TC ? tplan.nstage : plan.nstage;
+    const int nblk = (Ni + srows - 1) / srows;
 
     // the cell's sub-tet records arrive by one bulk copy while the state is loaded
     if (tid == 0) {
@@ -380,7 +533,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       }
     }
     // the padded columns of RHS stay zero (so do those of Y)
-    for (int e = tid; e < Ni * SRN; e += kF32Threads) srhs[e] = 0.f;
+    if constexpr (!TC)
+      for (int e = tid; e < Ni * SRN; e += kF32Threads) srhs[e] = 0.f;
     {
       const int64_t ib = m.inc_ptr[n0];
       const int ninc = (int)(m.inc_ptr[n0 + Ni] - ib);  // <= S * NP
@@ -395,7 +549,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     if (sAbort) {
       // a bulk copy that never completed: wait once more (bounded) for it, then leave
       if (tid == 0) (void)mbar_wait_bounded(&sbar, phase & 1u);
-      return;
+      goto kernel_exit;
     }
     (void)mbar_wait_bounded(&sbar, phase & 1u);  // completed: returns at once
     phase ^= 1u;
@@ -503,171 +657,47 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       } else {
         phase1(std::integral_constant<int, CH>{});
       }
+      if constexpr (!TC) {
 #pragma unroll
-      for (int r = 0; r < kF32Items; ++r) {
-        if (inode[r] < 0) continue;
-        const int t = (tid + r * kF32Threads) % NT;
+        for (int r = 0; r < kF32Items; ++r) {
+          if (inode[r] < 0) continue;
+          const int t = (tid + r * kF32Threads) % NT;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v * NTP + t] = racc[r][v];
-      }
-      // the ring reuses the phase-1 buffers: order this thread's generic-proxy accesses to
-      // them before the bulk copies (async proxy) that overwrite them
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      // ---- 2. Y = M_i^-1 RHS.  The last warp streams M_i^-1 through a ring of shared-memory
-      // stages (cp.async.bulk, full/empty mbarriers); the other warps never wait for each
-      // other inside the apply.  Consumer warp w accumulates the 16 x 8 tiles (mt, nt) of Y
-      // for mt = w, w + 15, w + 30 with 3xTF32 mma.sync; per 8-row k-step of a stage it loads
-      // the B fragments (RHS rows) once for all column tiles and the A fragments (M_i^-1
-      // rows = columns) once per row tile.
-      float cacc[3][NNT][4];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int nt = 0; nt < NNT; ++nt)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) cacc[r][nt][i] = 0.f;
-      if (!consumer) {
-        if (lane == 0) {
-          for (int b = 0; b < nblk && !sAbort; ++b) {
-            const int s = b % nstage;
-            if (b >= nstage) {
-              if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
-                atomicOr(&m.flags[F_TIMEOUT], 1);
-                sAbort = 1;
-                break;
-              }
-              epar ^= 1u << s;
-            }
-            const int rb = min(kF32Rows, Ni - b * kF32Rows);
-            mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
-            bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
-                     &sfull[s]);
-            issued |= 1u << s;
-            ipar ^= 1u << s;
-          }
-          // every stage released by the consumers before the ring is reused
-          for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
-            const int s = b % nstage;
-            if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
-              atomicOr(&m.flags[F_TIMEOUT], 1);
-              sAbort = 1;
-              break;
-            }
-            epar ^= 1u << s;
-          }
+          for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v * NTP + t] = racc[r][v];
         }
       } else {
-        for (int b = 0; b < nblk; ++b) {
-          const int s = b % nstage;
-          // lane 0 waits (bounded); the warp follows its verdict, so that no lane leaves the
-          // loop alone; the other lanes then observe the completed phase themselves
-          bool ok = true;
-          if (lane == 0) ok = mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          if (!ok) {
-            if (lane == 0) {
-              atomicOr(&m.flags[F_TIMEOUT], 1);
-              sAbort = 1;
-            }
-            break;
-          }
-          (void)mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
-          fpar ^= 1u << s;
-          const float* stage = ring + (size_t)s * stage_floats;
-          const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
-          // one 8-row k-step: B fragments (RHS rows) for every column tile, then per row tile the
-          // A fragments (M_i^-1 rows) and three rounds of MMAs over the column tiles
-          auto kstep = [&](int ks, bool full) {
-            const int k0 = ks * 8 + tq, k1 = k0 + 4;  // stage rows of this lane's fragments
-            const bool v0 = full || k0 < rb, v1 = full || k1 < rb;  // rows past N_i give zero
-            uint32_t bh[NNT][2], bl[NNT][2];
-#pragma unroll
-            for (int nt = 0; nt < NNT; ++nt) {
-              const float x0 = v0 ? srhs[(l0 + k0) * SRN + nt * 8 + gq] : 0.f;
-              const float x1 = v1 ? srhs[(l0 + k1) * SRN + nt * 8 + gq] : 0.f;
-              tf32_split(x0, bh[nt][0], bl[nt][0]);
-              tf32_split(x1, bh[nt][1], bl[nt][1]);
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              const int mt = warp + r * kF32Consumers;
-              if (mt >= nmt) break;
-              const float* arow0 = stage + k0 * LD + mt * 16 + gq;
-              const float* arow1 = stage + k1 * LD + mt * 16 + gq;
-              uint32_t ah[4], al[4];
-              tf32_split(v0 ? arow0[0] : 0.f, ah[0], al[0]);
-              tf32_split(v0 ? arow0[8] : 0.f, ah[1], al[1]);
-              tf32_split(v1 ? arow1[0] : 0.f, ah[2], al[2]);
-              tf32_split(v1 ? arow1[8] : 0.f, ah[3], al[3]);
-#pragma unroll
-              for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], al, bh[nt][0], bh[nt][1]);
-#pragma unroll
-              for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bl[nt][0], bl[nt][1]);
-#pragma unroll
-              for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bh[nt][0], bh[nt][1]);
-            }
-          };
-          if (rb == kF32Rows) {  // full stage: no row masks
-#pragma unroll
-            for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, true);
-          } else {
-#pragma unroll
-            for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, false);
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sempty[s]);
-        }
-      }
-      __syncthreads();  // every thread has finished reading RHS and the ring is drained
-      if (sAbort) {
-        // a bounded wait ran out (flags[F_TIMEOUT] is set): wait (bounded) for the last copy
-        // issued into every slot (the phase its completion ends), then leave
-        if (!consumer && lane == 0)
-          for (int s2 = 0; s2 < kF32MaxStages; ++s2)
-            if ((issued >> s2) & 1u) (void)mbar_wait_bounded(&sfull[s2], ((ipar >> s2) & 1u) ^ 1u);
+        // the right-hand-side operand B = [RHS | RHS - tf32(RHS)] (2 NB rows, K = the cell's
+        // nodes) aliases the last chunk's buffers: every thread has finished its gathers first
         __syncthreads();
-        return;
-      }
-      if (consumer)
+        constexpr int NB = tc_nb(N);
+        const int Kp = (Ni + 15) / 16 * 16;
+        auto bidx = [&](int n, int k) { return (n >> 3) * (Kp * 8) + (k >> 2) * 32 + (n & 7) * 4 + (k & 3); };
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int mt = warp + r * kF32Consumers;
-          if (mt >= nmt) break;
-          const int n0r = mt * 16 + gq, n1r = n0r + 8;
+        for (int r = 0; r < kF32Items; ++r) {
+          if (inode[r] < 0) continue;
+          const int t = (tid + r * kF32Threads) % NT;
 #pragma unroll
-          for (int nt = 0; nt < NNT; ++nt) {
-            const int col = nt * 8 + 2 * tq;
-            if (n0r < Ni) {
-              srhs[n0r * SRN + col] = cacc[r][nt][0];
-              srhs[n0r * SRN + col + 1] = cacc[r][nt][1];
-            }
-            if (n1r < Ni) {
-              srhs[n1r * SRN + col] = cacc[r][nt][2];
-              srhs[n1r * SRN + col + 1] = cacc[r][nt][3];
-            }
+          for (int v = 0; v < 5; ++v) {
+            const float x = racc[r][v];
+            bop[bidx(v * NTP + t, inode[r])] = x;
+            bop[bidx(NB + v * NTP + t, inode[r])] = x - tf32_trunc(x);
           }
         }
+        // rows without data (time slices past N+1, padding to NB) and columns past N_i: zero
+        for (int e = tid; e < 2 * NB * Kp; e += kF32Threads) {
+          const int n = e / Kp, k = e - (e / Kp) * Kp, nh = n % NB;
+          if (k >= Ni || nh >= 5 * NTP || nh % NTP >= NT) bop[bidx(n, k)] = 0.f;
+        }
+      }
+      // the ring reuses the phase-1 buffers: order this thread's generic-proxy accesses to
+      // them before the bulk copies (async proxy) that overwrite them; the tensor cores read
+      // the right-hand-side operand through the async proxy too
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       float res = 0.f, qmax = 0.f;
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int n = tid + r * kF32Threads;
-        if (n >= Ni) continue;
-        float y[NT][5], uh[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {  // one vector load per variable
-          float yv[NTP];
-          if constexpr (NTP == 4) {
-            const float4 w = *reinterpret_cast<const float4*>(srhs + n * SRN + v * 4);
-            yv[0] = w.x; yv[1] = w.y; yv[2] = w.z; yv[3] = w.w;
-          } else {
-            const float2 w = *reinterpret_cast<const float2*>(srhs + n * SRN + v * 2);
-            yv[0] = w.x; yv[1] = w.y;
-          }
-#pragma unroll
-          for (int t = 0; t < NT; ++t) y[t][v] = yv[t];
-        }
+      // q^{r+1}[n, s] = u^[n] - sum_t K1t^-1[s, t] Y[n, t], the residual and max |q^r|
+      auto update_node = [&](int n, const float (&y)[NT][5]) {
+        float uh[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) uh[v] = (float)m.u[(n0 + n) * 5 + v];  // u^ (L2-resident)
 #pragma unroll
@@ -682,6 +712,352 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             qmax = fmaxf(qmax, fabsf(old));
             sq[n * SR + s2 * 5 + v] = x;
           }
+      };
+      if constexpr (TC) {
+        // ---- 2. Y = M_i^-1 RHS on the tensor cores with tensor memory.  The last warp streams
+        // M_i^-1 through the ring of `srows`-row stages (as in the mma.sync form).  Three groups
+        // of four warps (one warp per 32-lane quarter of tensor memory) own the 128-row tiles
+        // T = g, g + 3 of Y: per slice of `SL` rows of a stage (= SL columns of M_i^-1 by
+        // symmetry) each thread moves its row's SL values into the tile's A buffer in tensor
+        // memory as TF32 value and remainder; lane 0 of the group's first warp then issues
+        // D_T += A_hi [B_hi | B_lo] + A_lo [B_hi | B_lo] per 8 columns and commits.  Several
+        // issuing warps keep the tensor core busy despite the narrow N.
+        constexpr int NB = tc_nb(N), NM = 2 * NB;
+        constexpr uint32_t IDESC = tc_idesc_tf32(NM);
+        const int SL = tplan.slice, spr = srows / SL, nsl = (Ni + SL - 1) / SL;
+        const int ntl = tplan.ntiles, nbuf = ntl <= kTcGroups ? 2 : 1;
+        const uint32_t sbo = (uint32_t)((Ni + 15) / 16 * 16) * 32u;
+        const uint32_t bsh = smem_u32(bop);
+        auto acol = [&](int T, int b) { return (uint32_t)(kTcACol0 + (T * nbuf + b) * 32); };
+        if (warp == kF32Warps - 1) {
+          if (lane == 0) {
+            for (int b = 0; b < nblk && !sAbort; ++b) {
+              const int s = b % nstage;
+              if (b >= nstage) {
+                if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+                  atomicOr(&m.flags[F_TIMEOUT], 1);
+                  sAbort = 1;
+                  break;
+                }
+                epar ^= 1u << s;
+              }
+              const int rb = min(srows, Ni - b * srows);
+              mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
+              bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
+                       &sfull[s]);
+              issued |= 1u << s;
+              ipar ^= 1u << s;
+            }
+            for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
+              const int s = b % nstage;
+              if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+                atomicOr(&m.flags[F_TIMEOUT], 1);
+                sAbort = 1;
+                break;
+              }
+              epar ^= 1u << s;
+            }
+          }
+        } else if (warp < kTcStagers) {
+          const int g = warp >> 2, qq = warp & 3;
+          const bool issuer = qq == 0 && lane == 0;
+          for (int s = 0; s < nsl; ++s) {
+            if (*(volatile int*)&sAbort) break;
+            const int b = s / spr, sl = s - b * spr, slot = b % nstage;
+            const int rb = min(srows, Ni - b * srows);
+            bool ok = true;
+            if (sl == 0) {  // the stage has arrived
+              if (lane == 0) ok = mbar_wait_bounded(&sfull[slot], (fpar >> slot) & 1u);
+              ok = __shfl_sync(0xffffffffu, ok, 0);
+              if (!ok) {
+                if (lane == 0) {
+                  atomicOr(&m.flags[F_TIMEOUT], 1);
+                  sAbort = 1;
+                }
+                break;
+              }
+              (void)mbar_wait_bounded(&sfull[slot], (fpar >> slot) & 1u);
+              fpar ^= 1u << slot;
+            }
+            const float* stage = ring + (size_t)slot * stage_floats;
+            const int buf = nbuf == 2 ? (s & 1) : 0;
+            for (int T = g; T < ntl; T += kTcGroups) {
+              const int bi = T * 2 + buf;
+              if ((aever >> bi) & 1u) {  // the MMAs that last read this A buffer have completed
+                if (lane == 0) ok = mbar_wait_bounded(&saempty[bi], ((acnt >> bi) & 1u) ^ 1u);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                (void)mbar_wait_bounded(&saempty[bi], ((acnt >> bi) & 1u) ^ 1u);
+                tc_fence_after();
+              }
+              const int mrow = T * 128 + qq * 32 + lane;
+              const bool live = mrow < Ni;
+              float hv[16], lv[16];
+#pragma unroll
+              for (int kk = 0; kk < 16; ++kk) {
+                float x = 0.f;
+                if (kk < SL && live && sl * SL + kk < rb) x = stage[(sl * SL + kk) * LD + mrow];
+                hv[kk] = x;
+                lv[kk] = x - tf32_trunc(x);
+              }
+              const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + acol(T, buf);
+              tmem_st8(ta, hv);
+              tmem_st8(ta + 16, lv);
+              if (SL == 16) {
+                tmem_st8(ta + 8, hv + 8);
+                tmem_st8(ta + 24, lv + 8);
+              }
+            }
+            if (!ok) {
+              if (lane == 0) {
+                atomicOr(&m.flags[F_TIMEOUT], 1);
+                sAbort = 1;
+              }
+              break;
+            }
+            tmem_st_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              for (int T = g; T < ntl; T += kTcGroups) mbar_arrive(&safull[T * 2 + buf]);
+              if (sl == spr - 1 || s == nsl - 1) mbar_arrive(&sempty[slot]);  // stage read
+            }
+            if (issuer) {
+              for (int T = g; T < ntl; T += kTcGroups) {
+                const int bi = T * 2 + buf;
+                if (!mbar_wait_bounded(&safull[bi], (afp >> bi) & 1u)) {
+                  atomicOr(&m.flags[F_TIMEOUT], 1);
+                  sAbort = 1;
+                  ok = false;
+                  break;
+                }
+                afp ^= 1u << bi;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(T * kTcDCols);
+                const uint32_t a = tmem + acol(T, buf);
+                for (int j = 0; j < SL / 8; ++j) {
+                  const int k0 = s * SL + 8 * j;
+                  const uint64_t bd = tc_sdesc(bsh + (uint32_t)k0 * 32u, 128u, sbo);
+                  tc_mma_tmem_a(d, a + 8 * j, bd, IDESC, (s | j) != 0 ? 1u : 0u);
+                  tc_mma_tmem_a(d, a + 16 + 8 * j, bd, IDESC, 1u);
+                }
+                tc_commit(&saempty[bi]);
+              }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            for (int T = g; T < ntl; T += kTcGroups) {  // the group follows the issuer's commits
+              acnt ^= 1u << (T * 2 + buf);
+              aever |= 1u << (T * 2 + buf);
+            }
+            if (!ok) break;
+          }
+          if (issuer && !*(volatile int*)&sAbort)
+            for (int T = g; T < ntl; T += kTcGroups) tc_commit(&sdfull[T]);
+        }
+        __syncthreads();
+        if (sAbort) {
+          // a bounded wait ran out: wait (bounded) for the ring's copies in flight and for every
+          // issuer's MMAs, then leave
+          if (warp == kF32Warps - 1 && lane == 0)
+            for (int s2 = 0; s2 < kF32MaxStages; ++s2)
+              if ((issued >> s2) & 1u) (void)mbar_wait_bounded(&sfull[s2], ((ipar >> s2) & 1u) ^ 1u);
+          if (warp < kTcStagers && (warp & 3) == 0 && lane == 0) {
+            tc_commit(&sdrain[warp >> 2]);
+            (void)mbar_wait_bounded(&sdrain[warp >> 2], 0u);
+          }
+          __syncthreads();
+          goto kernel_exit;
+        }
+        // Y from the accumulators: thread (group g, quarter qq, lane) holds node T*128 + qq*32 + lane
+        if (warp < kTcStagers) {
+          const int g = warp >> 2, qq = warp & 3;
+          for (int T = g; T < ntl; T += kTcGroups) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&sdfull[T], (dpar >> T) & 1u);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+              if (lane == 0) {
+                atomicOr(&m.flags[F_TIMEOUT], 1);
+                sAbort = 1;
+              }
+              break;
+            }
+            (void)mbar_wait_bounded(&sdfull[T], (dpar >> T) & 1u);
+            dpar ^= 1u << T;
+            tc_fence_after();
+            float dv[48];
+            const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + (uint32_t)(T * kTcDCols);
+            tmem_ld16(ta, dv);
+            tmem_ld16(ta + 16, dv + 16);
+            if constexpr (NM > 32) tmem_ld16(ta + 32, dv + 32);
+            const int n = T * 128 + qq * 32 + lane;
+            if (n < Ni) {
+              float y[NT][5];
+#pragma unroll
+              for (int v = 0; v < 5; ++v)
+#pragma unroll
+                for (int t = 0; t < NT; ++t) y[t][v] = dv[v * NTP + t] + dv[NB + v * NTP + t];
+              update_node(n, y);
+            }
+          }
+          tc_fence_before();
+        }
+      } else {
+        // ---- 2. Y = M_i^-1 RHS.  The last warp streams M_i^-1 through a ring of shared-memory
+        // stages (cp.async.bulk, full/empty mbarriers); the other warps never wait for each
+        // other inside the apply.  Consumer warp w accumulates the 16 x 8 tiles (mt, nt) of Y
+        // for mt = w, w + 15, w + 30 with 3xTF32 mma.sync; per 8-row k-step of a stage it loads
+        // the B fragments (RHS rows) once for all column tiles and the A fragments (M_i^-1
+        // rows = columns) once per row tile.
+        float cacc[3][NNT][4];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int nt = 0; nt < NNT; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) cacc[r][nt][i] = 0.f;
+        if (!consumer) {
+          if (lane == 0) {
+            for (int b = 0; b < nblk && !sAbort; ++b) {
+              const int s = b % nstage;
+              if (b >= nstage) {
+                if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+                  atomicOr(&m.flags[F_TIMEOUT], 1);
+                  sAbort = 1;
+                  break;
+                }
+                epar ^= 1u << s;
+              }
+              const int rb = min(srows, Ni - b * srows);
+              mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
+              bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
+                       &sfull[s]);
+              issued |= 1u << s;
+              ipar ^= 1u << s;
+            }
+            // every stage released by the consumers before the ring is reused
+            for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
+              const int s = b % nstage;
+              if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+                atomicOr(&m.flags[F_TIMEOUT], 1);
+                sAbort = 1;
+                break;
+              }
+              epar ^= 1u << s;
+            }
+          }
+        } else {
+          for (int b = 0; b < nblk; ++b) {
+            const int s = b % nstage;
+            // lane 0 waits (bounded); the warp follows its verdict, so that no lane leaves the
+            // loop alone; the other lanes then observe the completed phase themselves
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+              if (lane == 0) {
+                atomicOr(&m.flags[F_TIMEOUT], 1);
+                sAbort = 1;
+              }
+              break;
+            }
+            (void)mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
+            fpar ^= 1u << s;
+            const float* stage = ring + (size_t)s * stage_floats;
+            const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
+            // one 8-row k-step: B fragments (RHS rows) for every column tile, then per row tile the
+            // A fragments (M_i^-1 rows) and three rounds of MMAs over the column tiles
+            auto kstep = [&](int ks, bool full) {
+              const int k0 = ks * 8 + tq, k1 = k0 + 4;  // stage rows of this lane's fragments
+              const bool v0 = full || k0 < rb, v1 = full || k1 < rb;  // rows past N_i give zero
+              uint32_t bh[NNT][2], bl[NNT][2];
+#pragma unroll
+              for (int nt = 0; nt < NNT; ++nt) {
+                const float x0 = v0 ? srhs[(l0 + k0) * SRN + nt * 8 + gq] : 0.f;
+                const float x1 = v1 ? srhs[(l0 + k1) * SRN + nt * 8 + gq] : 0.f;
+                tf32_split(x0, bh[nt][0], bl[nt][0]);
+                tf32_split(x1, bh[nt][1], bl[nt][1]);
+              }
+#pragma unroll
+              for (int r = 0; r < 3; ++r) {
+                const int mt = warp + r * kF32Consumers;
+                if (mt >= nmt) break;
+                const float* arow0 = stage + k0 * LD + mt * 16 + gq;
+                const float* arow1 = stage + k1 * LD + mt * 16 + gq;
+                uint32_t ah[4], al[4];
+                tf32_split(v0 ? arow0[0] : 0.f, ah[0], al[0]);
+                tf32_split(v0 ? arow0[8] : 0.f, ah[1], al[1]);
+                tf32_split(v1 ? arow1[0] : 0.f, ah[2], al[2]);
+                tf32_split(v1 ? arow1[8] : 0.f, ah[3], al[3]);
+#pragma unroll
+                for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], al, bh[nt][0], bh[nt][1]);
+#pragma unroll
+                for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bl[nt][0], bl[nt][1]);
+#pragma unroll
+                for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bh[nt][0], bh[nt][1]);
+              }
+            };
+            if (rb == kF32Rows) {  // full stage: no row masks
+#pragma unroll
+              for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, true);
+            } else {
+#pragma unroll
+              for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, false);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sempty[s]);
+          }
+        }
+        __syncthreads();  // every thread has finished reading RHS and the ring is drained
+        if (sAbort) {
+          // a bounded wait ran out (flags[F_TIMEOUT] is set): wait (bounded) for the last copy
+          // issued into every slot (the phase its completion ends), then leave
+          if (!consumer && lane == 0)
+            for (int s2 = 0; s2 < kF32MaxStages; ++s2)
+              if ((issued >> s2) & 1u) (void)mbar_wait_bounded(&sfull[s2], ((ipar >> s2) & 1u) ^ 1u);
+          __syncthreads();
+          goto kernel_exit;
+        }
+        if (consumer)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const int mt = warp + r * kF32Consumers;
+            if (mt >= nmt) break;
+            const int n0r = mt * 16 + gq, n1r = n0r + 8;
+#pragma unroll
+            for (int nt = 0; nt < NNT; ++nt) {
+              const int col = nt * 8 + 2 * tq;
+              if (n0r < Ni) {
+                srhs[n0r * SRN + col] = cacc[r][nt][0];
+                srhs[n0r * SRN + col + 1] = cacc[r][nt][1];
+              }
+              if (n1r < Ni) {
+                srhs[n1r * SRN + col] = cacc[r][nt][2];
+                srhs[n1r * SRN + col + 1] = cacc[r][nt][3];
+              }
+            }
+          }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int n = tid + r * kF32Threads;
+          if (n >= Ni) continue;
+          float y[NT][5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {  // one vector load per variable
+            float yv[NTP];
+            if constexpr (NTP == 4) {
+              const float4 w = *reinterpret_cast<const float4*>(srhs + n * SRN + v * 4);
+              yv[0] = w.x; yv[1] = w.y; yv[2] = w.z; yv[3] = w.w;
+            } else {
+              const float2 w = *reinterpret_cast<const float2*>(srhs + n * SRN + v * 2);
+              yv[0] = w.x; yv[1] = w.y;
+            }
+#pragma unroll
+            for (int t = 0; t < NT; ++t) y[t][v] = yv[t];
+          }
+          update_node(n, y);
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -693,6 +1069,16 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         sred[1][warp] = qmax;
       }
       __syncthreads();
+      if constexpr (TC) {
+        if (sAbort) {  // an accumulator never completed: drain every issuer's MMAs and leave
+          if (warp < kTcStagers && (warp & 3) == 0 && lane == 0) {
+            tc_commit(&sdrain[warp >> 2]);
+            (void)mbar_wait_bounded(&sdrain[warp >> 2], 0u);
+          }
+          __syncthreads();
+          goto kernel_exit;
+        }
+      }
       res = 0.f;
       qmax = 0.f;
 #pragma unroll
@@ -864,6 +1250,13 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         m.qbar_diag[(n0 + n) * 5 + v] = (double)dt * (double)acc;
       }
     __syncthreads();
+  }
+kernel_exit:
+  if constexpr (TC) {  // every path out of the cell loop ends here: release the tensor memory
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kTcCols);
   }
 }
 

@@ -78,16 +78,25 @@ def test_fp32_limiter_against_the_oracle(afe):
     pr.close()
 
 
-def test_fp32_large_cells_take_narrow_chunks_and_a_one_stage_ring(afe):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp32_large_cells_take_narrow_chunks_and_a_one_stage_ring(afe, variant):
     """Two cubes whose edges are split (4, 4, 3): 88 sub-tets and 623 nodes per cell at N = 3,
-    the largest the shared-memory plan takes with 8-sub-tet chunks and a single 32-row stage
-    of M_i^-1 (623 = 19 * 32 + 15, so the last stage is partial)."""
+    the largest the shared-memory plan takes with 8-sub-tet chunks and a single stage of
+    M_i^-1 (32 rows in the mma.sync form, fewer in the tensor-memory form, whose right-hand
+    side takes more room); 623 is not a multiple of the stage height, so the last stage is
+    partial.  Both forms of the apply (variant 0: tcgen05 / tensor memory, five 128-row
+    tiles; variant 1: mma.sync)."""
     pm = split_cube_lattice((2, 1, 1), (4, 4, 3), d=0.5)
     p = _fp32(afe, 3)
     pr = Pair(pm, p)
+    afe.afe_set_predictor_variant(pr.h, variant)
     plan = afe.afe_plan_info(pr.h)
+    print(f"plan variant {variant}: tcgen05 {plan.tcgen05} smem {plan.smem_bytes} ring {plan.ring_min}-"
+          f"{plan.ring_max} rows {plan.stage_rows_min} narrow {plan.narrow_cells} masked {plan.masked_cells}")
     assert plan.fp32_shared == 1 and plan.max_nodes == 623 and plan.max_subtets == 88
+    assert plan.tcgen05 == (1 if variant == 0 else 0)
     assert plan.narrow_cells == 2 and plan.ring_min == 1 and plan.masked_cells == 2
+    assert plan.stage_rows_min == (32 if variant == 1 else plan.stage_rows_min) and plan.stage_rows_min < 32 + 32 * variant
     x = pr.om.node_coords()
     pr.set_state(states.density_wave(x, amp=0.1, vel=(0.5, -0.3, 0.2)))
     _steps(pr, 3)
@@ -116,9 +125,15 @@ def test_plan_report_of_a_voronoi_mesh(afe):
     plan = afe.afe_plan_info(h)
     ptr = afe.afe_node_ptr(h, pm.n_cells)
     Ni = np.diff(ptr)
-    assert plan.fp32_shared == 1 and plan.max_nodes == Ni.max()
+    assert plan.fp32_shared == 1 and plan.max_nodes == Ni.max() and plan.tcgen05 == 1
     assert 1 <= plan.ring_min <= plan.ring_max <= 8
+    assert plan.masked_cells == int(np.sum(Ni % plan.stage_rows_min != 0)) and plan.narrow_cells == 0
+    afe.afe_set_predictor_variant(h, 1)
+    plan = afe.afe_plan_info(h)
+    assert plan.tcgen05 == 0 and plan.stage_rows_min == 32
     assert plan.masked_cells == int(np.sum(Ni % 32 != 0)) and plan.narrow_cells == 0
+    with pytest.raises(afe.AfeError):
+        afe.afe_set_predictor_variant(h, 2)
     afe.afe_mesh_destroy(h)
     h = afe.create_from_polymesh(pm, afe.afe_default_params(3))
     assert afe.afe_plan_info(h).fp32_shared == 0 and afe.afe_plan_info(h).smem_bytes == 0
@@ -144,4 +159,31 @@ def test_bounded_wait_gives_up_and_reports_timeout(afe):
     pr.set_state(states.density_wave(pr.om.node_coords()))
     _steps(pr, 2)
     assert rel_l2(pr.lib_state(), pr.u) <= FP32_TOL
+    pr.close()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_tensor_memory_and_mma_sync_forms_agree(afe, N):
+    """The two forms of the M_i^-1 apply (tcgen05 with tensor memory, and mma.sync) compute the
+    same 3xTF32 product: after 3 steps of the density wave they agree to FP32 rounding, and
+    each meets the oracle bar."""
+    pm = periodic_voronoi(3 if N < 3 else 2)
+    p = _fp32(afe, N)
+    pr = Pair(pm, p)
+    h1 = afe.create_from_polymesh(pm, p)
+    afe.afe_set_predictor_variant(h1, 1)
+    assert afe.afe_plan_info(pr.h).tcgen05 == 1 and afe.afe_plan_info(h1).tcgen05 == 0
+    u0 = states.density_wave(pr.om.node_coords())
+    pr.set_state(u0)
+    afe.afe_set_state(h1, u0[pr.perm])
+    for _ in range(3):
+        info = pr.oracle_step()
+        assert pr.lib_step(info.dt) == 0
+        assert afe.afe_step(h1, info.dt) == 0
+    a = pr.lib_state()
+    b = np.empty_like(a)
+    b[pr.perm] = afe.afe_get_state(h1)
+    assert rel_l2(a, b) <= 1e-6
+    assert rel_l2(a, pr.u) <= FP32_TOL and rel_l2(b, pr.u) <= FP32_TOL
+    afe.afe_mesh_destroy(h1)
     pr.close()
