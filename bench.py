@@ -65,6 +65,8 @@ def _args():
     ap.add_argument("--visc-dt", default="subtet", choices=["subtet", "cell"],
                     help="shock/tgv: length in the viscous term of the time step (the smallest "
                          "sub-tet length, or the cell length as printed; see the stokes study)")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1],
+                    help="FP32 predictor's M_i^-1 apply: 0 mma.sync, 1 tcgen05 with tensor memory")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
     ap.add_argument("--study", choices=["convergence", "stokes", "vortex", "shock"], help="accuracy study instead of the throughput run")
     ap.add_argument("--workload", default="density", choices=["density", "shock", "tgv"],
@@ -435,6 +437,8 @@ def ours(args):
         p = afe.afe_default_params(args.order, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
                                    picard_max=128 if fp32 else 64, cfl=cfl, **extra)
         h = afe.create_from_polymesh(pm, p, stream=sid)
+        if prec == afe.AFE_FP32:
+            afe.afe_set_predictor_variant(h, args.variant)
         n_nodes = afe.afe_num_nodes(h)
         node_ptr = afe.afe_node_ptr(h, pm.n_cells)
         x = afe.afe_get_node_coords(h)

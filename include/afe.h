@@ -214,11 +214,12 @@ typedef struct {
 } afe_plan;
 afe_status afe_plan_info(const afe_mesh* m, afe_plan* out);
 
-/* Which form of the FP32 predictor's M_i^-1 apply a handle uses: 0 (the default) takes the
- * tensor-memory form (tcgen05) whenever every cell fits its shared-memory plan (up to 640
- * nodes per cell), else the mma.sync form; 1 always takes the mma.sync form.  Both compute
- * the same 3xTF32 product (results agree to FP32 rounding, not bit for bit).  A batch takes
- * the tensor-memory form unless one of its members asks for 1.  Other values: AFE_EINVAL. */
+/* Which form of the FP32 predictor's M_i^-1 apply a handle uses: 0 (the default) the
+ * warp-level mma.sync form; 1 the form on the 5th-generation tensor cores with tensor memory
+ * (tcgen05), for meshes whose every cell fits its shared-memory plan (up to 640 nodes per cell;
+ * else AFE_EINVAL).  Both compute the same 3xTF32 product (results agree to FP32 rounding, not
+ * bit for bit); on the measured workloads the mma.sync form is the faster one.  A batch takes
+ * the tensor-memory form only when every member asks for it.  Other values: AFE_EINVAL. */
 afe_status afe_set_predictor_variant(afe_mesh* m, int32_t variant);
 
 /* Poll limit of the first bounded wait the FP32 shared-memory predictor makes for every cell

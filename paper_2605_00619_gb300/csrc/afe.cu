@@ -52,7 +52,7 @@ struct afe_mesh {
   int f32_ok = 0;        // the shared-memory FP32 predictor is used
   int f32_tc = 0;        // ... with its M_i^-1 apply on tcgen05 / tensor memory (else mma.sync)
   int f32_tc_fits = 0;   // every cell fits the tensor-memory plan
-  int variant = 0;       // 0: automatic, 1: mma.sync apply
+  int variant = 0;       // 0: mma.sync apply, 1: tcgen05 / tensor memory where the cells fit
   size_t f32_smem = 0;
   double* d_totals_partial = nullptr;
   double* d_totals = nullptr;
@@ -151,8 +151,8 @@ void launch_predictor(const StepPlan& P) {
 }
 
 // Shared-memory plan of the FP32 predictor; cells too large for it use the global-scratch kernel.
-// The M_i^-1 apply runs on tcgen05 / tensor memory when every cell fits that plan (and the
-// handle does not ask for the mma.sync form), else on mma.sync.
+// The M_i^-1 apply runs on mma.sync unless the handle asks for the tcgen05 / tensor-memory
+// form and every cell fits that plan.
 template <int N>
 afe_status plan_f32(afe_mesh* m) {
   cudaFuncAttributes fa, fb;
@@ -172,7 +172,7 @@ afe_status plan_f32(afe_mesh* m) {
   m->f32_ok = 1;
   m->f32_smem = b;
   m->f32_tc_fits = afe::tc_cell_plan(N, b, m->dm.Smax, m->dm.Nmax).ok ? 1 : 0;
-  m->f32_tc = (m->f32_tc_fits && m->variant == 0) ? 1 : 0;
+  m->f32_tc = (m->f32_tc_fits && m->variant == 1) ? 1 : 0;
   AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)b));
   AFE_CUDA(cudaFuncSetAttribute(afe::predictor_f32_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -784,9 +784,11 @@ afe_status afe_plan_info(const afe_mesh* m, afe_plan* out) {
 
 afe_status afe_set_predictor_variant(afe_mesh* m, int32_t variant) {
   if (!m) return fail(AFE_EINVAL, "NULL mesh");
-  if (variant != 0 && variant != 1) return fail(AFE_EINVAL, "variant must be 0 (automatic) or 1 (mma.sync)");
+  if (variant != 0 && variant != 1) return fail(AFE_EINVAL, "variant must be 0 (mma.sync) or 1 (tcgen05)");
+  if (variant == 1 && m->p.precision == AFE_FP32 && !(m->f32_ok && m->f32_tc_fits))
+    return fail(AFE_EINVAL, "the cells do not fit the tensor-memory plan of the FP32 predictor");
   m->variant = variant;
-  m->f32_tc = (m->f32_ok && m->f32_tc_fits && variant == 0) ? 1 : 0;
+  m->f32_tc = (m->f32_ok && m->f32_tc_fits && variant == 1) ? 1 : 0;
   return AFE_OK;
 }
 
@@ -928,7 +930,7 @@ afe_status afe_batch_create(afe_mesh* const* members, int n_members, void* cuda_
   P.f32_smem = m0->f32_smem;
   P.f32_tc = afe::tc_cell_plan(P.order, P.f32_smem, Smax, Nmax).ok ? 1 : 0;
   for (afe_mesh* m : b->mem)
-    if (m->variant != 0) P.f32_tc = 0;
+    if (m->variant != 1) P.f32_tc = 0;
   P.d_ref = m0->d_ref;
   P.single = nullptr;
   P.prof = nullptr;

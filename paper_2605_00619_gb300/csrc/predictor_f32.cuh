@@ -61,15 +61,32 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One test of an mbarrier phase.  The waiting thread may be suspended until the phase
+// completes or a time limit passes: the hardware's own, or about kWaitHintNs nanoseconds when
+// that is set (a hint of 32 or 1000 ns measured no different from none on these kernels).
+#ifndef AFE_WAIT_HINT_NS
+#define AFE_WAIT_HINT_NS 0
+#endif
+constexpr uint32_t kWaitHintNs = AFE_WAIT_HINT_NS;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if constexpr (kWaitHintNs == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
+        : "memory");
+  }
   return ok != 0;
 }
 
@@ -187,6 +204,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
                "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
                : "memory");
 }
+__device__ __forceinline__ void tmem_st8v(uint32_t taddr, float a0, float a1, float a2, float a3, float a4, float a5,
+                                          float a6, float a7) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "f"(a0),
+               "f"(a1), "f"(a2), "f"(a3), "f"(a4), "f"(a5), "f"(a6), "f"(a7)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // 16 consecutive columns, waiting for the load in the same statement (the registers are
 // valid only after the wait)
@@ -196,6 +219,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
       "%15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
       : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
         "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
       : "r"(taddr)
       : "memory");
 }
@@ -278,8 +309,11 @@ constexpr int kTcMaxTiles = 5;      // 128-row tiles: cells of up to 640 nodes
 constexpr int kTcGroups = 3;        // groups of 4 warps that stage M_i^-1 and read Y
 constexpr int kTcStagers = 4 * kTcGroups;
 constexpr int kTcDCols = 48;        // tensor-memory columns per accumulator (2 NB <= 48)
-constexpr int kTcACol0 = kTcMaxTiles * kTcDCols;  // first column of the A staging buffers
+constexpr int kTcBufs = 3;          // most A staging buffers per tile
 constexpr int kTcCols = 512;
+// A staging buffers per tile for a cell of `ntiles` tiles: as many as the 512 columns hold
+// after the accumulators (32 columns each: TF32 value and remainder of 16 rows)
+__host__ __device__ constexpr int tc_nbuf(int ntiles) { return ntiles <= 3 ? 3 : (ntiles == 4 ? 2 : 1); }
 // Bytes of the right-hand-side operand: 2 NB rows x Kp (N_i rounded up to 16) TF32 words.
 __host__ __device__ inline size_t tc_bop_bytes(int N, int Ni) {
   const size_t Kp = (size_t)(Ni + 15) / 16 * 16;
@@ -400,8 +434,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   __shared__ int64_t sCell;
   // tensor-memory form: per (tile, buffer) "A staged" and "MMAs done reading A", per tile
   // "accumulator complete", per staging group a drain barrier; the tensor-memory address
-  __shared__ __align__(8) uint64_t safull[TC ? 2 * kTcMaxTiles : 1];
-  __shared__ __align__(8) uint64_t saempty[TC ? 2 * kTcMaxTiles : 1];
+  __shared__ __align__(8) uint64_t safull[TC ? kTcBufs * kTcMaxTiles : 1];
+  __shared__ __align__(8) uint64_t saempty[TC ? kTcBufs * kTcMaxTiles : 1];
   __shared__ __align__(8) uint64_t sdfull[TC ? kTcMaxTiles : 1];
   __shared__ __align__(8) uint64_t sdrain[TC ? kTcGroups : 1];
   __shared__ uint32_t stmem;
@@ -440,7 +474,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       mbar_init(&sempty[i], TC ? kTcStagers : kF32Consumers);
     }
     if constexpr (TC) {
-      for (int i = 0; i < 2 * kTcMaxTiles; ++i) {
+      for (int i = 0; i < kTcBufs * kTcMaxTiles; ++i) {
         mbar_init(&safull[i], 4);
         mbar_init(&saempty[i], 1);
       }
@@ -551,7 +585,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       if (tid == 0) (void)mbar_wait_bounded(&sbar, phase & 1u);
       goto kernel_exit;
     }
-    (void)mbar_wait_bounded(&sbar, phase & 1u);  // completed: returns at once
+    // thread 0 observed the copy's completion (acquire); the barrier above orders the records
+    // for every thread (a wait by all 512 threads would be 512 serialised barrier tests)
     phase ^= 1u;
     __syncthreads();
 
@@ -719,16 +754,18 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         // of four warps (one warp per 32-lane quarter of tensor memory) own the 128-row tiles
         // T = g, g + 3 of Y: per slice of `SL` rows of a stage (= SL columns of M_i^-1 by
         // symmetry) each thread moves its row's SL values into the tile's A buffer in tensor
-        // memory as TF32 value and remainder; lane 0 of the group's first warp then issues
+        // memory as TF32 value and remainder (up to three buffers per tile in turn); a
+        // dedicated issuing warp per group (warps 12 - 14) then issues
         // D_T += A_hi [B_hi | B_lo] + A_lo [B_hi | B_lo] per 8 columns and commits.  Several
         // issuing warps keep the tensor core busy despite the narrow N.
         constexpr int NB = tc_nb(N), NM = 2 * NB;
         constexpr uint32_t IDESC = tc_idesc_tf32(NM);
         const int SL = tplan.slice, spr = srows / SL, nsl = (Ni + SL - 1) / SL;
-        const int ntl = tplan.ntiles, nbuf = ntl <= kTcGroups ? 2 : 1;
+        const int ntl = tplan.ntiles, nbuf = tc_nbuf(ntl);
         const uint32_t sbo = (uint32_t)((Ni + 15) / 16 * 16) * 32u;
         const uint32_t bsh = smem_u32(bop);
-        auto acol = [&](int T, int b) { return (uint32_t)(kTcACol0 + (T * nbuf + b) * 32); };
+        // tensor-memory columns: accumulators T * 48, then the A buffers (32 columns each)
+        auto acol = [&](int T, int b) { return (uint32_t)(ntl * kTcDCols + (T * nbuf + b) * 32); };
         if (warp == kF32Warps - 1) {
           if (lane == 0) {
             for (int b = 0; b < nblk && !sAbort; ++b) {
@@ -759,8 +796,8 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             }
           }
         } else if (warp < kTcStagers) {
+          // staging warps: group g = warp / 4 owns tiles g, g + 3; warp quarter qq = warp % 4
           const int g = warp >> 2, qq = warp & 3;
-          const bool issuer = qq == 0 && lane == 0;
           for (int s = 0; s < nsl; ++s) {
             if (*(volatile int*)&sAbort) break;
             const int b = s / spr, sl = s - b * spr, slot = b % nstage;
@@ -776,37 +813,41 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
                 }
                 break;
               }
-              (void)mbar_wait_bounded(&sfull[slot], (fpar >> slot) & 1u);
+              __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
               fpar ^= 1u << slot;
             }
             const float* stage = ring + (size_t)slot * stage_floats;
-            const int buf = nbuf == 2 ? (s & 1) : 0;
+            const int buf = s % nbuf;
             for (int T = g; T < ntl; T += kTcGroups) {
-              const int bi = T * 2 + buf;
+              const int bi = T * kTcBufs + buf;
               if ((aever >> bi) & 1u) {  // the MMAs that last read this A buffer have completed
                 if (lane == 0) ok = mbar_wait_bounded(&saempty[bi], ((acnt >> bi) & 1u) ^ 1u);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) break;
-                (void)mbar_wait_bounded(&saempty[bi], ((acnt >> bi) & 1u) ^ 1u);
+                __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
                 tc_fence_after();
               }
               const int mrow = T * 128 + qq * 32 + lane;
-              const bool live = mrow < Ni;
-              float hv[16], lv[16];
-#pragma unroll
-              for (int kk = 0; kk < 16; ++kk) {
-                float x = 0.f;
-                if (kk < SL && live && sl * SL + kk < rb) x = stage[(sl * SL + kk) * LD + mrow];
-                hv[kk] = x;
-                lv[kk] = x - tf32_trunc(x);
-              }
               const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + acol(T, buf);
-              tmem_st8(ta, hv);
-              tmem_st8(ta + 16, lv);
+              // the slice's columns k of this thread's row of M_i^-1: every shared-memory load
+              // first, then the tensor-memory stores (a load issued behind a store waits for it)
+              const int kend = (mrow < Ni) ? min(SL, rb - sl * SL) : 0;
+              const float* src = stage + (size_t)(sl * SL) * LD + mrow;
+              float x[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) x[i] = (i < kend) ? src[i * LD] : 0.f;
+              tmem_st8v(ta, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7]);
+              tmem_st8v(ta + 16, x[0] - tf32_trunc(x[0]), x[1] - tf32_trunc(x[1]), x[2] - tf32_trunc(x[2]),
+                        x[3] - tf32_trunc(x[3]), x[4] - tf32_trunc(x[4]), x[5] - tf32_trunc(x[5]),
+                        x[6] - tf32_trunc(x[6]), x[7] - tf32_trunc(x[7]));
               if (SL == 16) {
-                tmem_st8(ta + 8, hv + 8);
-                tmem_st8(ta + 24, lv + 8);
+                tmem_st8v(ta + 8, x[8], x[9], x[10], x[11], x[12], x[13], x[14], x[15]);
+                tmem_st8v(ta + 24, x[8] - tf32_trunc(x[8]), x[9] - tf32_trunc(x[9]), x[10] - tf32_trunc(x[10]),
+                          x[11] - tf32_trunc(x[11]), x[12] - tf32_trunc(x[12]), x[13] - tf32_trunc(x[13]),
+                          x[14] - tf32_trunc(x[14]), x[15] - tf32_trunc(x[15]));
               }
+              acnt ^= 1u << bi;  // the issuer commits once per tile and slice
+              aever |= 1u << bi;
             }
             if (!ok) {
               if (lane == 0) {
@@ -819,39 +860,43 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-              for (int T = g; T < ntl; T += kTcGroups) mbar_arrive(&safull[T * 2 + buf]);
+              for (int T = g; T < ntl; T += kTcGroups) mbar_arrive(&safull[T * kTcBufs + buf]);
               if (sl == spr - 1 || s == nsl - 1) mbar_arrive(&sempty[slot]);  // stage read
             }
-            if (issuer) {
-              for (int T = g; T < ntl; T += kTcGroups) {
-                const int bi = T * 2 + buf;
-                if (!mbar_wait_bounded(&safull[bi], (afp >> bi) & 1u)) {
-                  atomicOr(&m.flags[F_TIMEOUT], 1);
-                  sAbort = 1;
-                  ok = false;
-                  break;
-                }
-                afp ^= 1u << bi;
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(T * kTcDCols);
-                const uint32_t a = tmem + acol(T, buf);
-                for (int j = 0; j < SL / 8; ++j) {
-                  const int k0 = s * SL + 8 * j;
-                  const uint64_t bd = tc_sdesc(bsh + (uint32_t)k0 * 32u, 128u, sbo);
-                  tc_mma_tmem_a(d, a + 8 * j, bd, IDESC, (s | j) != 0 ? 1u : 0u);
-                  tc_mma_tmem_a(d, a + 16 + 8 * j, bd, IDESC, 1u);
-                }
-                tc_commit(&saempty[bi]);
-              }
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            for (int T = g; T < ntl; T += kTcGroups) {  // the group follows the issuer's commits
-              acnt ^= 1u << (T * 2 + buf);
-              aever |= 1u << (T * 2 + buf);
-            }
-            if (!ok) break;
           }
-          if (issuer && !*(volatile int*)&sAbort)
+        } else if (warp < kTcStagers + kTcGroups && lane == 0) {
+          // issuing thread of group g: per slice and tile, once the four staging warps have
+          // filled the A buffer, D_T += A_hi [B_hi | B_lo] + A_lo [B_hi | B_lo] per 8 columns
+          const int g = warp - kTcStagers;
+          for (int s = 0; s < nsl; ++s) {
+            if (*(volatile int*)&sAbort) break;
+            const int buf = s % nbuf;
+            bool ok = true;
+            for (int T = g; T < ntl; T += kTcGroups) {
+              const int bi = T * kTcBufs + buf;
+              if (!mbar_wait_bounded(&safull[bi], (afp >> bi) & 1u)) {
+                ok = false;
+                break;
+              }
+              afp ^= 1u << bi;
+              tc_fence_after();
+              const uint32_t d = tmem + (uint32_t)(T * kTcDCols);
+              const uint32_t a = tmem + acol(T, buf);
+              for (int j = 0; j < SL / 8; ++j) {
+                const int k0 = s * SL + 8 * j;
+                const uint64_t bd = tc_sdesc(bsh + (uint32_t)k0 * 32u, 128u, sbo);
+                tc_mma_tmem_a(d, a + 8 * j, bd, IDESC, (s | j) != 0 ? 1u : 0u);
+                tc_mma_tmem_a(d, a + 16 + 8 * j, bd, IDESC, 1u);
+              }
+              tc_commit(&saempty[bi]);
+            }
+            if (!ok) {
+              atomicOr(&m.flags[F_TIMEOUT], 1);
+              sAbort = 1;
+              break;
+            }
+          }
+          if (!*(volatile int*)&sAbort)
             for (int T = g; T < ntl; T += kTcGroups) tc_commit(&sdfull[T]);
         }
         __syncthreads();
@@ -861,9 +906,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           if (warp == kF32Warps - 1 && lane == 0)
             for (int s2 = 0; s2 < kF32MaxStages; ++s2)
               if ((issued >> s2) & 1u) (void)mbar_wait_bounded(&sfull[s2], ((ipar >> s2) & 1u) ^ 1u);
-          if (warp < kTcStagers && (warp & 3) == 0 && lane == 0) {
-            tc_commit(&sdrain[warp >> 2]);
-            (void)mbar_wait_bounded(&sdrain[warp >> 2], 0u);
+          if (warp >= kTcStagers && warp < kTcStagers + kTcGroups && lane == 0) {
+            tc_commit(&sdrain[warp - kTcStagers]);
+            (void)mbar_wait_bounded(&sdrain[warp - kTcStagers], 0u);
           }
           __syncthreads();
           goto kernel_exit;
@@ -882,21 +927,27 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
               }
               break;
             }
-            (void)mbar_wait_bounded(&sdfull[T], (dpar >> T) & 1u);
+            __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
             dpar ^= 1u << T;
             tc_fence_after();
-            float dv[48];
             const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + (uint32_t)(T * kTcDCols);
-            tmem_ld16(ta, dv);
-            tmem_ld16(ta + 16, dv + 16);
-            if constexpr (NM > 32) tmem_ld16(ta + 32, dv + 32);
+            // Y column c = v NTP + t is D[:, c] + D[:, NB + c]; eight columns at a time
+            float yf[NB];
+#pragma unroll
+            for (int c = 0; c < NB; c += 8) {
+              float hi[8], lo[8];
+              tmem_ld8(ta + c, hi);
+              tmem_ld8(ta + NB + c, lo);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) yf[c + i] = hi[i] + lo[i];
+            }
             const int n = T * 128 + qq * 32 + lane;
             if (n < Ni) {
               float y[NT][5];
 #pragma unroll
               for (int v = 0; v < 5; ++v)
 #pragma unroll
-                for (int t = 0; t < NT; ++t) y[t][v] = dv[v * NTP + t] + dv[NB + v * NTP + t];
+                for (int t = 0; t < NT; ++t) y[t][v] = yf[v * NTP + t];
               update_node(n, y);
             }
           }
@@ -950,7 +1001,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           for (int b = 0; b < nblk; ++b) {
             const int s = b % nstage;
             // lane 0 waits (bounded); the warp follows its verdict, so that no lane leaves the
-            // loop alone; the other lanes then observe the completed phase themselves
+            // loop alone
             bool ok = true;
             if (lane == 0) ok = mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -961,7 +1012,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
               }
               break;
             }
-            (void)mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
+            __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
             fpar ^= 1u << s;
             const float* stage = ring + (size_t)s * stage_floats;
             const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
@@ -1071,9 +1122,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       __syncthreads();
       if constexpr (TC) {
         if (sAbort) {  // an accumulator never completed: drain every issuer's MMAs and leave
-          if (warp < kTcStagers && (warp & 3) == 0 && lane == 0) {
-            tc_commit(&sdrain[warp >> 2]);
-            (void)mbar_wait_bounded(&sdrain[warp >> 2], 0u);
+          if (warp >= kTcStagers && warp < kTcStagers + kTcGroups && lane == 0) {
+            tc_commit(&sdrain[warp - kTcStagers]);
+            (void)mbar_wait_bounded(&sdrain[warp - kTcStagers], 0u);
           }
           __syncthreads();
           goto kernel_exit;

@@ -232,3 +232,19 @@ def test_served_requests_match_the_oracle(afe, meshes):
         assert rel_l2(r.q, ref) <= 1e-5, f"request {r.rid}"
     afe.afe_mesh_destroy(h)
     eng.close()
+
+
+def test_batch_in_the_tensor_memory_form_equals_alone(afe, meshes):
+    """Members that ask for the tcgen05 / tensor-memory form of the M_i^-1 apply make the
+    batch take it; each member still equals stepping it alone in that form, bit for bit."""
+    mem = _members(afe, meshes)
+    for h, _ in mem:
+        afe.afe_set_predictor_variant(h, 1)
+        assert afe.afe_plan_info(h).tcgen05 == 1
+    ref = _alone(afe, mem, 3)
+    got, statuses, _ = _batched(afe, mem, [1, 2], True)
+    for i, ((qa, dta, sta), (qb, dtb)) in enumerate(zip(ref, got)):
+        np.testing.assert_array_equal(qb, qa, err_msg=f"member {i}")
+        assert dta == dtb and statuses[i] == sta
+    for h, _ in mem:
+        afe.afe_mesh_destroy(h)

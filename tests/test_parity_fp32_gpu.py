@@ -46,13 +46,16 @@ def _steps(pr, n, allowed=(0,)):
     return infos
 
 
-def test_fp32_navier_stokes_against_the_oracle(afe):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp32_navier_stokes_against_the_oracle(afe, variant):
     """Navier-Stokes Taylor-Green data (mu 0.005, kappa from Pr): the FP32 viscous flux with
-    per-sub-tet gradients in the predictor and the face-node fluxes."""
+    per-sub-tet gradients in the predictor and the face-node fluxes (both forms of the
+    M_i^-1 apply)."""
     pm = periodic_voronoi(2)
     p = _fp32(afe, 2, equations=afe.AFE_NAVIER_STOKES, mu=0.005, kappa=-1.0, Pr=0.71)
     pr = Pair(pm, p)
-    assert afe.afe_plan_info(pr.h).fp32_shared == 1
+    afe.afe_set_predictor_variant(pr.h, variant)
+    assert afe.afe_plan_info(pr.h).fp32_shared == 1 and afe.afe_plan_info(pr.h).tcgen05 == variant
     pr.set_state(states.taylor_green_3d(2 * math.pi * pr.om.node_coords(), p0=10.0))
     _steps(pr, 3)
     # w vanishes at t = 0: the momentum is compared as one vector field
@@ -80,12 +83,11 @@ def test_fp32_limiter_against_the_oracle(afe):
 
 @pytest.mark.parametrize("variant", [0, 1])
 def test_fp32_large_cells_take_narrow_chunks_and_a_one_stage_ring(afe, variant):
-    """Two cubes whose edges are split (4, 4, 3): 88 sub-tets and 623 nodes per cell at N = 3,
-    the largest the shared-memory plan takes with 8-sub-tet chunks and a single stage of
-    M_i^-1 (32 rows in the mma.sync form, fewer in the tensor-memory form, whose right-hand
-    side takes more room); 623 is not a multiple of the stage height, so the last stage is
-    partial.  Both forms of the apply (variant 0: tcgen05 / tensor memory, five 128-row
-    tiles; variant 1: mma.sync)."""
+    """Two cubes whose edges are split (4, 4, 3): 88 sub-tets and 623 nodes per cell at N = 3.
+    The mma.sync form (variant 0) takes 8-sub-tet chunks and a single 32-row stage of M_i^-1;
+    the tensor-memory form (variant 1, five 128-row tiles, single-buffered tensor memory)
+    takes a single 8-row stage.  623 is not a multiple of either, so the last stage is
+    partial."""
     pm = split_cube_lattice((2, 1, 1), (4, 4, 3), d=0.5)
     p = _fp32(afe, 3)
     pr = Pair(pm, p)
@@ -94,9 +96,12 @@ def test_fp32_large_cells_take_narrow_chunks_and_a_one_stage_ring(afe, variant):
     print(f"plan variant {variant}: tcgen05 {plan.tcgen05} smem {plan.smem_bytes} ring {plan.ring_min}-"
           f"{plan.ring_max} rows {plan.stage_rows_min} narrow {plan.narrow_cells} masked {plan.masked_cells}")
     assert plan.fp32_shared == 1 and plan.max_nodes == 623 and plan.max_subtets == 88
-    assert plan.tcgen05 == (1 if variant == 0 else 0)
-    assert plan.narrow_cells == 2 and plan.ring_min == 1 and plan.masked_cells == 2
-    assert plan.stage_rows_min == (32 if variant == 1 else plan.stage_rows_min) and plan.stage_rows_min < 32 + 32 * variant
+    assert plan.tcgen05 == variant
+    assert plan.ring_min == 1 and plan.masked_cells == 2
+    if variant == 0:  # q and RHS rows leave too little room for 16-sub-tet chunks
+        assert plan.narrow_cells == 2 and plan.stage_rows_min == 32
+    else:  # no RHS rows, but the two-part right-hand-side operand leaves room for 8-row stages only
+        assert plan.narrow_cells == 0 and plan.stage_rows_min == 8
     x = pr.om.node_coords()
     pr.set_state(states.density_wave(x, amp=0.1, vel=(0.5, -0.3, 0.2)))
     _steps(pr, 3)
@@ -125,13 +130,14 @@ def test_plan_report_of_a_voronoi_mesh(afe):
     plan = afe.afe_plan_info(h)
     ptr = afe.afe_node_ptr(h, pm.n_cells)
     Ni = np.diff(ptr)
-    assert plan.fp32_shared == 1 and plan.max_nodes == Ni.max() and plan.tcgen05 == 1
+    assert plan.fp32_shared == 1 and plan.max_nodes == Ni.max() and plan.tcgen05 == 0
     assert 1 <= plan.ring_min <= plan.ring_max <= 8
-    assert plan.masked_cells == int(np.sum(Ni % plan.stage_rows_min != 0)) and plan.narrow_cells == 0
+    assert plan.stage_rows_min == 32 and plan.narrow_cells == 0
+    assert plan.masked_cells == int(np.sum(Ni % 32 != 0))
     afe.afe_set_predictor_variant(h, 1)
     plan = afe.afe_plan_info(h)
-    assert plan.tcgen05 == 0 and plan.stage_rows_min == 32
-    assert plan.masked_cells == int(np.sum(Ni % 32 != 0)) and plan.narrow_cells == 0
+    assert plan.tcgen05 == 1 and 1 <= plan.ring_min <= plan.ring_max <= 8
+    assert plan.masked_cells == int(np.sum(Ni % plan.stage_rows_min != 0)) and plan.narrow_cells == 0
     with pytest.raises(afe.AfeError):
         afe.afe_set_predictor_variant(h, 2)
     afe.afe_mesh_destroy(h)
@@ -171,7 +177,7 @@ def test_tensor_memory_and_mma_sync_forms_agree(afe, N):
     p = _fp32(afe, N)
     pr = Pair(pm, p)
     h1 = afe.create_from_polymesh(pm, p)
-    afe.afe_set_predictor_variant(h1, 1)
+    afe.afe_set_predictor_variant(pr.h, 1)
     assert afe.afe_plan_info(pr.h).tcgen05 == 1 and afe.afe_plan_info(h1).tcgen05 == 0
     u0 = states.density_wave(pr.om.node_coords())
     pr.set_state(u0)
