@@ -10,7 +10,7 @@ corrector).  ``value`` is the reduced-precision form (FP32 arithmetic, FP64 mast
 FP64 time step and conservative cell totals); the plain FP64 form is timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --serve      (continuous-batching serving run; see serve())
+  python bench.py --serve      (continuous-batching serving run alone; see run_serving())
 
 N > 1 (torchrun): every rank runs an independent simulation (mesh seed = rank); there is
 no data-path collective and ``value`` is the sum over ranks of DOF-updates over the max
@@ -75,12 +75,13 @@ def _args():
                          "[0,2pi)^3, mu 0.01")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=50.0, help="offered load, requests per second")
-    ap.add_argument("--serve-steps", type=int, default=20, help="CFL steps per request")
+    ap.add_argument("--serve-steps", type=int, default=100, help="CFL steps per request")
     ap.add_argument("--serve-slots", type=int, default=4, help="slots per catalogue entry (mesh, N)")
     ap.add_argument("--serve-elastic", type=float, default=None, metavar="BYTES",
                     help="admit by device footprint within BYTES instead of fixed slot pools")
-    ap.add_argument("--serve-limiter", action="store_true",
-                    help="explosion requests with the limiter and the sub-tet viscous time step")
+    ap.add_argument("--serve-no-limiter", dest="serve_limiter", action="store_false",
+                    help="explosion requests without the limiter (they may end non-finite)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving record of the throughput run")
     return ap.parse_args()
 
 
@@ -553,6 +554,14 @@ def ours(args):
         out["fp32_over_fp64"] = value / out["fp64_plain"]["value"]
         if args.workload == "density":
             out["fp32_over_fp64_accuracy"] = equal_steps_accuracy(args.order, cfl)
+    if rank == 0 and world == 1 and not args.no_serving and args.workload == "density":
+        # bounded serving record: 64 requests of 100 steps on 8^3 - 16^3 meshes; the serial
+        # FP64 comparison runs the first 16 of them
+        try:
+            out["serving"] = run_serving(64, 50.0, 100, serial_requests=16)
+            out["serving"].pop("clocks", None)
+        except Exception as e:  # the serving record never hides the throughput line
+            out["serving"] = {"error": str(e)[:300]}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             n_s, rec = oracle_sample(args.order, 1, cfl)
@@ -578,24 +587,23 @@ def ours(args):
         dist.destroy_process_group()
 
 
-def serve(args):
-    """Continuous batching of many independent simulations (one GPU).
+def run_serving(n_req, rate, steps, sizes=(8, 12, 16), limiter=True, slots_per_key=4, elastic_bytes=None,
+                serial_requests=None, ratio=(2.0, 20.0), seed=12345):
+    """Continuous batching of many independent simulations on one GPU; returns one record.
 
-    Requests (after the serving workload of the method's evaluation, scaled to resident
-    meshes): a mesh drawn uniformly from a catalogue of jittered-Voronoi meshes -- the periodic
-    unit cube and the box [-1,1]^3, 8^3 and 12^3 seeds -- with N uniform in {1, 2, 3}; the
-    periodic meshes carry the density wave, the box meshes a spherical explosion smoothed
-    over 1.5 lattice spacings with a random centre in [-0.5,0.5]^3 and pressure ratio in
-    [2, 10] (no limiter by default: with the artificial viscosity and the printed viscous
-    time step these runs diverge within a few steps on the fan-subgrid meshes;
-    ``--serve-limiter`` turns the limiter on together with the sub-tet viscous time step); each
-    request runs ``--serve-steps`` CFL steps.  ``--serve-elastic BYTES`` starts the batched
-    server with no slots and admits requests by device footprint within BYTES (idle slots of
-    other meshes evicted least recently used first) instead of fixed pools.  Arrivals are a Poisson process of
-    ``--serve-rate`` per second.  The batched server (FP32 form; every occupied slot advanced
-    together, one launch per stage and order, a CUDA graph per batch) is timed against the
-    serial server running the same requests one at a time in the plain FP64 form.  Reported:
-    DOF-updates/s over each run and p50/p99 request latency (arrival to completion).
+    Requests follow the serving workload of the method's evaluation, scaled to resident
+    meshes: a mesh drawn uniformly from a catalogue of jittered-Voronoi meshes -- the periodic
+    unit cube and the box [-1,1]^3 with ``sizes`` seeds per direction -- with N uniform in
+    {1, 2, 3}; periodic meshes carry the density wave, box meshes a spherical explosion
+    smoothed over 1.5 lattice spacings with a random centre in [-0.5,0.5]^3 and a pressure
+    ratio uniform in ``ratio`` (with the limiter and the sub-tet viscous time step when
+    ``limiter``); each request runs ``steps`` CFL steps.  Arrivals: a Poisson process of
+    ``rate`` per second (seeded).  The catalogue's meshes and slots are built before the
+    arrival clock starts.  The batched server (FP32 form; every occupied slot advanced together,
+    one launch per stage and order, a CUDA graph per batch) runs every request; the serial
+    server runs the first ``serial_requests`` (all by default) one at a time in the plain FP64
+    form, so that its DOF-updates/s compare rate with rate.  ``elastic_bytes`` admits by device
+    footprint within that budget instead of fixed pools of ``slots_per_key`` slots.
     """
     import numpy as np
     import torch
@@ -605,9 +613,7 @@ def serve(args):
     from paper_2605_00619_gb300 import afe
     from paper_2605_00619_gb300.serving import GpuEngine, Request, Server
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     afe.lib()
-    sizes = (8, 12)
     meshes = {}
     for n in sizes:
         meshes[f"p{n}"] = periodic_voronoi(n, seed=100 + n)
@@ -615,67 +621,81 @@ def serve(args):
 
     def params(kind, N, prec):
         fp32 = prec == afe.AFE_FP32
-        extra = dict(limiter=1, visc_dt_subtet=1) if kind == "b" and args.serve_limiter else {}
+        extra = dict(limiter=1, visc_dt_subtet=1) if kind == "b" and limiter else {}
         return afe.afe_default_params(N, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
                                       picard_max=128 if fp32 else 64, cfl=STABLE_CFL[N], **extra)
 
     keys = [f"{mk}_N{N}" for mk in sorted(meshes) for N in (1, 2, 3)]
     cat32 = {k: (meshes[k.split("_")[0]], params(k[0], int(k[-1]), afe.AFE_FP32)) for k in keys}
     cat64 = {k: (meshes[k.split("_")[0]], params(k[0], int(k[-1]), afe.AFE_FP64)) for k in keys}
-    elastic = args.serve_elastic is not None
-    eng = (GpuEngine(cat32, {}, budget_bytes=int(args.serve_elastic)) if elastic
-           else GpuEngine(cat32, {k: args.serve_slots for k in keys}))
+    elastic = elastic_bytes is not None
+    t_setup = time.perf_counter()
+    eng = (GpuEngine(cat32, {}, budget_bytes=int(elastic_bytes)) if elastic
+           else GpuEngine(cat32, {k: slots_per_key for k in keys}))
     ser = GpuEngine(cat64, {k: 1 for k in keys})
+    t_setup = time.perf_counter() - t_setup
+    rng = np.random.default_rng(seed)
 
-    rng = np.random.default_rng(12345)
-
-    def make_requests(n_req, rate):
+    def make_requests(count, r):
         out, t = [], 0.0
-        for i in range(n_req):
-            t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        for i in range(count):
+            t += rng.exponential(1.0 / r) if r > 0 else 0.0
             k = keys[int(rng.integers(len(keys)))]
             if k.startswith("p"):
                 ic = states.density_wave
             else:
                 c = rng.uniform(-0.5, 0.5, 3)
-                ratio = rng.uniform(2.0, 10.0)
+                pr = rng.uniform(*ratio)
                 a0 = 1.5 * 2.0 / int(k.split("_")[0][1:])  # smoothing width: 1.5 lattice spacings
                 ic = (lambda c_, r_, a_: lambda x: states.spherical_riemann(x, centre=tuple(c_), p_in=0.1 * r_,
-                                                                             alpha0=a_))(c, ratio, a0)
-            out.append(Request(i, k, args.serve_steps, t, q0=ic))
+                                                                             alpha0=a_))(c, pr, a0)
+            out.append(Request(i, k, steps, t, q0=ic))
         return out
 
     Server(eng, elastic=elastic).run(make_requests(len(keys) if elastic else len(eng.slots), 0.0))  # warm-up
     Server(ser, mode="serial").run(make_requests(len(keys), 0.0))
-    reqs = make_requests(args.serve_requests, args.serve_rate)
+    reqs = make_requests(n_req, rate)
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     srv = Server(eng, max_chunk=8, elastic=elastic)
     sb = srv.run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
     clk = clocks.stop()
-    ss = Server(ser, mode="serial").run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in reqs])
+    sub = reqs[:serial_requests] if serial_requests else reqs
+    ss = Server(ser, mode="serial").run([Request(r.rid, r.mesh, r.nsteps, r.arrival, q0=r.q0) for r in sub])
     out = {
         "metric": "serving throughput, continuous batching (FP32) vs serial plain FP64", "value": sb.throughput,
         "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-        "p50_ms": 1e3 * sb.p50_s, "p99_ms": 1e3 * sb.p99_s, "mean_ms": 1e3 * sb.mean_s,
+        "requests": sb.requests, "p50_ms": 1e3 * sb.p50_s, "p99_ms": 1e3 * sb.p99_s, "mean_ms": 1e3 * sb.mean_s,
         "mean_batch_members": sb.mean_batch, "batch_steps": sb.steps_launched, "failed": sb.failed,
         "makespan_s": sb.makespan_s,
-        "serial_fp64": {"value": ss.throughput, "unit": UNIT, "p50_ms": 1e3 * ss.p50_s, "p99_ms": 1e3 * ss.p99_s,
-                        "makespan_s": ss.makespan_s, "failed": ss.failed},
+        "serial_fp64": {"value": ss.throughput, "unit": UNIT, "requests": ss.requests, "p50_ms": 1e3 * ss.p50_s,
+                        "p99_ms": 1e3 * ss.p99_s, "makespan_s": ss.makespan_s, "failed": ss.failed,
+                        "note": "the same requests one at a time in the plain FP64 form"
+                                + (f" (the first {len(sub)} of {len(reqs)}: DOF-updates/s compare as rates)"
+                                   if len(sub) < len(reqs) else "")},
         "batched_over_serial": sb.throughput / ss.throughput,
         "clocks": clk,
-        "config": {"workload": f"{args.serve_requests} requests, Poisson arrivals at {args.serve_rate:g}/s, "
-                               f"{args.serve_steps} CFL steps each; meshes periodic/box {sizes[0]}^3 and "
-                               f"{sizes[1]}^3, N in {{1,2,3}}; density wave (periodic) or smoothed spherical "
-                               f"explosion, pressure ratio 2-10 (box)",
-                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes,
-                   "admission": (f"elastic within {int(args.serve_elastic)} bytes: {srv.slots_added} slots made, "
+        "config": {"workload": f"{n_req} requests, Poisson arrivals at {rate:g}/s, {steps} CFL steps each; meshes "
+                               f"periodic/box {', '.join(f'{n}^3' for n in sizes)}, N in {{1,2,3}}; density wave "
+                               f"(periodic) or smoothed spherical explosion, pressure ratio {ratio[0]:g}-{ratio[1]:g} "
+                               f"(box)", "catalogue_keys": len(keys),
+                   "slots": len(eng.slots), "pool_device_bytes": eng.device_bytes, "setup_s": t_setup,
+                   "admission": (f"elastic within {int(elastic_bytes)} bytes: {srv.slots_added} slots made, "
                                  f"{srv.slots_evicted} evicted") if elastic else "fixed slot pools",
-                   "limiter_on_explosions": bool(args.serve_limiter)},
+                   "limiter_on_explosions": bool(limiter)},
     }
     eng.close()
     ser.close()
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def serve(args):
+    """``--serve``: the serving run alone (see run_serving) with the command-line settings."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    print(json.dumps(run_serving(args.serve_requests, args.serve_rate, args.serve_steps,
+                                 limiter=args.serve_limiter, slots_per_key=args.serve_slots,
+                                 elastic_bytes=args.serve_elastic)), flush=True)
 
 
 def convergence(args):

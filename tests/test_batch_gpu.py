@@ -248,3 +248,34 @@ def test_batch_in_the_tensor_memory_form_equals_alone(afe, meshes):
         assert dta == dtb and statuses[i] == sta
     for h, _ in mem:
         afe.afe_mesh_destroy(h)
+
+
+def test_elastic_serving_results_equal_alone(afe, meshes):
+    """Elastic admission on the GPU: the pool starts empty and a budget of about two slots of
+    the larger mesh forces slots to be made, and evicted once the requests for their mesh are
+    done; every request still ends with exactly the state of stepping it alone."""
+    from paper_2605_00619_gb300.serving import GpuEngine, Request, Server
+    p = afe.afe_default_params(2, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+    cat = {"a": meshes["a"], "c": meshes["c"]}
+    probe = GpuEngine(cat, {}, p)
+    budget = 2 * probe.footprint("c") + probe.footprint("a") // 2
+    probe.close()
+    eng = GpuEngine(cat, {}, p, budget_bytes=budget)
+    ics = {"a": states.density_wave, "c": lambda x: states.constant(x, vel=(0.1, 0.2, 0.3))}
+    keys = ["c"] * 4 + ["a"] * 4  # the 'a' requests find the budget taken by 'c' slots, evicted once idle
+    reqs = [Request(i, k, 2 + i % 3, 0.0, q0=ics[k]) for i, k in enumerate(keys)]
+    srv = Server(eng, max_chunk=2, keep_results=True, elastic=True)
+    stats = srv.run(reqs)
+    assert stats.requests == 8 and stats.failed == 0
+    assert srv.slots_added >= 2 and srv.slots_evicted >= 1
+    assert eng.device_bytes <= budget
+    solo = {k: afe.create_from_polymesh(pm, p) for k, pm in cat.items()}
+    for r in reqs:
+        h = solo[r.mesh]
+        afe.afe_set_state(h, ics[r.mesh](afe.afe_get_node_coords(h)))
+        afe.afe_step_async(h, 0.0, r.nsteps)
+        assert afe.afe_sync(h, check=False) == 0
+        np.testing.assert_array_equal(r.q, afe.afe_get_state(h), err_msg=f"request {r.rid}")
+    for h in solo.values():
+        afe.afe_mesh_destroy(h)
+    eng.close()
