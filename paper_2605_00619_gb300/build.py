@@ -56,7 +56,7 @@ def build(verbose: bool = False, extra_flags=None) -> str:
             if o.strip():
                 print(o)
     objs = [j[-1] for j in jobs]
-    _run([nvcc, "-shared", *ARCH, "-o", LIBPATH, *objs, "-lpthread"])
+    _run([nvcc, "-shared", *ARCH, "-o", LIBPATH, *objs, "-lpthread", "-ldl"])
     return LIBPATH
 
 

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "afe.h"
 #include "kernels.cuh"
 #include "predictor_f32.cuh"
@@ -19,6 +21,13 @@
 namespace {
 
 thread_local std::string g_err;
+
+// Named NVTX range around the host-side enqueue of a stage (visible to Nsight Systems and
+// other NVTX tools, which correlate it with the kernels it launches; a no-op without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 afe_status fail(afe_status s, const std::string& msg) {
   g_err = msg;
@@ -267,15 +276,28 @@ afe_status record(const StepPlan& P) {
 int launches_per_step(const StepPlan& P, double dt) { return 1 + (P.limiter ? 2 : 0) + (dt > 0 ? 1 : 2) + 3 + 1; }
 
 afe_status enqueue_step(const StepPlan& P, double dt) {
+  NvtxRange step_range("afe step");
   afe::step_begin_kernel<<<1, 64, 0, P.st>>>(*P.b);
   AFE_TRY(record(P));
-  AFE_TRY(enqueue_dt(P, dt));
+  {
+    NvtxRange r("afe limiter + time step");
+    AFE_TRY(enqueue_dt(P, dt));
+  }
   AFE_TRY(record(P));
-  AFE_TRY(stage(P, 0));
+  {
+    NvtxRange r("afe predictor");
+    AFE_TRY(stage(P, 0));
+  }
   AFE_TRY(record(P));
-  AFE_TRY(stage(P, 1));
+  {
+    NvtxRange r("afe face fluxes");
+    AFE_TRY(stage(P, 1));
+  }
   AFE_TRY(record(P));
-  AFE_TRY(stage(P, 2));
+  {
+    NvtxRange r("afe corrector");
+    AFE_TRY(stage(P, 2));
+  }
   AFE_TRY(record(P));
   afe::advance_time_kernel<<<1, 64, 0, P.st>>>(*P.b);
   AFE_CUDA(cudaGetLastError());
@@ -509,6 +531,7 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
     }
   }
   // FP64 set-up on the GPU: mass matrices, w_i, inverses
+  NvtxRange setup_range("afe set-up: mass matrices and inverses");
   AFE_CUDA(cudaMemsetAsync(d.flags, 0, afe::F_COUNT * sizeof(int), M->stream));
   const int sgrid = (int)std::min<int64_t>(T.C, (int64_t)M->n_sm * 4);
   afe::assemble_mass_kernel<<<sgrid, 256, 0, M->stream>>>(d, M->d_ref);
