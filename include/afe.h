@@ -231,6 +231,40 @@ afe_status afe_set_predictor_variant(afe_mesh* m, int32_t variant);
  * polls < 0 returns AFE_EINVAL. */
 afe_status afe_set_wait_limit(afe_mesh* m, int32_t polls);
 
+/* How the FP32 shared-memory predictor schedules its work; the paper has no counterpart (it
+ * concerns the launch, not the method).  Every setting leaves each cell's arithmetic unchanged
+ * except `variant`, so results are bit for bit the same across cost_order, ring_cap and narrow.
+ *   cost_order  1: the persistent predictor blocks take cells in decreasing order of their
+ *               estimated cost per fixed-point iteration (S Nt Np (155 + 30 Np) + 10 Nt N_i^2
+ *               flops; ties in index order), so that the last cells of a launch are cheap ones
+ *               and the blocks finish together (the cells of a batch are bucketed by cost across
+ *               its members); 0: index order.
+ *   variant     0: mma.sync form of the M_i^-1 apply; 1: tcgen05 / tensor-memory form (only if
+ *               every cell fits its plan; see afe_set_predictor_variant).
+ *   ring_cap    most M_i^-1 stages in flight in the ring (0: as many as fit, at most 8).
+ *   narrow      1: right-hand side in chunks of 8 sub-tets even where 16 fit.
+ * Other values: AFE_EINVAL. */
+typedef struct {
+  int32_t cost_order;
+  int32_t variant;
+  int32_t ring_cap;
+  int32_t narrow;
+} afe_schedule;
+afe_status afe_set_schedule(afe_mesh* m, const afe_schedule* s);
+afe_status afe_get_schedule(const afe_mesh* m, afe_schedule* s);
+
+/* Choose the schedule by measurement: with the time step of the current state computed on the
+ * device, every candidate (cost_order 0/1; variant 0, and 1 where the cells fit; ring_cap 0 or
+ * 2; narrow 0, and 1 where wide chunks are used) times `trials` launches of the predictor alone
+ * (CUDA events on the handle's stream; the predictor writes only per-step intermediates, so
+ * the state is unchanged), and the fastest is set.  *best receives it, *best_ms and
+ * *default_ms (either may be NULL) the mean predictor time with it and with the default
+ * schedule {0, 0, 0, 0}.  The choice is remembered per mesh signature (order, cells and their
+ * node and sub-tet counts) for this process: a later call on an equal mesh only sets it.
+ * Synchronises the stream.  FP32 handles with the shared-memory predictor only (else
+ * AFE_EINVAL); trials in 1..64. */
+afe_status afe_autotune(afe_mesh* m, int trials, afe_schedule* best, double* best_ms, double* default_ms);
+
 /* Conserved totals of a caller-provided device state, with no device memory allocated by the
  * call.  The paper has no counterpart: this serves callers that must not call cudaMalloc at
  * the point of use, e.g. code running inside a framework whose caching allocator owns all
@@ -288,6 +322,13 @@ afe_status afe_batch_step_async(afe_batch* b, double dt, int nsteps, int use_gra
  * AFE_ETIMEOUT); the return value is the most severe of them.  Each member's time, step
  * count and last dt (afe_get_stats) are brought up to date. */
 afe_status afe_batch_sync(afe_batch* b, int* member_status);
+
+/* The schedule of a batch's predictor (see afe_schedule; the cost order runs over the cells of
+ * all members together) and its measured choice (as afe_autotune, on the batch).  Setting a
+ * schedule drops the batch's captured graph (it is captured again on the next step). */
+afe_status afe_batch_set_schedule(afe_batch* b, const afe_schedule* s);
+afe_status afe_batch_autotune(afe_batch* b, int trials, afe_schedule* best, double* best_ms,
+                              double* default_ms);
 
 /* Total cells and nodes of the members, kernels launched so far (counted one by one, also
  * when they ran inside graphs) and graph launches (NULL to skip any). */

@@ -75,6 +75,15 @@ class afe_plan(ctypes.Structure):
     ]
 
 
+class afe_schedule(ctypes.Structure):
+    _fields_ = [
+        ("cost_order", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
+        ("ring_cap", ctypes.c_int32),
+        ("narrow", ctypes.c_int32),
+    ]
+
+
 class AfeError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {message}")
@@ -114,6 +123,11 @@ _SIGS = {
     "afe_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(afe_plan)]),
     "afe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32]),
     "afe_set_predictor_variant": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "afe_set_schedule": (ctypes.c_int, [_P, ctypes.POINTER(afe_schedule)]),
+    "afe_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(afe_schedule)]),
+    "afe_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(afe_schedule), _D, _D]),
+    "afe_batch_set_schedule": (ctypes.c_int, [_P, ctypes.POINTER(afe_schedule)]),
+    "afe_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(afe_schedule), _D, _D]),
     "afe_stage_times": (ctypes.c_int, [_P, _D, _I64, ctypes.c_int]),
     "afe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "afe_batch_step_async": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
@@ -314,6 +328,42 @@ def afe_plan_info(m) -> afe_plan:
 
 def afe_set_predictor_variant(m, variant: int):
     _check(lib().afe_set_predictor_variant(m, int(variant)))
+
+
+def _schedule(cost_order=0, variant=0, ring_cap=0, narrow=0) -> afe_schedule:
+    return afe_schedule(int(cost_order), int(variant), int(ring_cap), int(narrow))
+
+
+def afe_set_schedule(m, cost_order=0, variant=0, ring_cap=0, narrow=0, check: bool = True) -> int:
+    s = _schedule(cost_order, variant, ring_cap, narrow)
+    return _check(lib().afe_set_schedule(m, ctypes.byref(s)), check)
+
+
+def afe_get_schedule(m) -> afe_schedule:
+    s = afe_schedule()
+    _check(lib().afe_get_schedule(m, ctypes.byref(s)))
+    return s
+
+
+def afe_autotune(m, trials: int = 3):
+    """Returns (chosen schedule, mean predictor ms with it, with the default; -1 when the choice
+    came from the remembered signature)."""
+    s = afe_schedule()
+    b, d = ctypes.c_double(), ctypes.c_double()
+    _check(lib().afe_autotune(m, int(trials), ctypes.byref(s), ctypes.byref(b), ctypes.byref(d)))
+    return s, b.value, d.value
+
+
+def afe_batch_set_schedule(b, cost_order=0, variant=0, ring_cap=0, narrow=0, check: bool = True) -> int:
+    s = _schedule(cost_order, variant, ring_cap, narrow)
+    return _check(lib().afe_batch_set_schedule(b, ctypes.byref(s)), check)
+
+
+def afe_batch_autotune(b, trials: int = 3):
+    s = afe_schedule()
+    x, d = ctypes.c_double(), ctypes.c_double()
+    _check(lib().afe_batch_autotune(b, int(trials), ctypes.byref(s), ctypes.byref(x), ctypes.byref(d)))
+    return s, x.value, d.value
 
 
 def afe_set_wait_limit(m, polls: int):

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -62,6 +63,8 @@ struct afe_mesh {
   int f32_tc = 0;        // ... with its M_i^-1 apply on tcgen05 / tensor memory (else mma.sync)
   int f32_tc_fits = 0;   // every cell fits the tensor-memory plan
   int variant = 0;       // 0: mma.sync apply, 1: tcgen05 / tensor memory where the cells fit
+  afe_schedule sched{};  // predictor schedule (cost order, ring cap, narrow chunks; variant above)
+  int32_t* d_order = nullptr;  // the cells in decreasing cost (allocated when first asked for)
   size_t f32_smem = 0;
   double* d_totals_partial = nullptr;
   double* d_totals = nullptr;
@@ -328,6 +331,9 @@ afe_status status_of(const int* flags) {
 // Refreshes the batch-of-one record read by the batch-aware kernels.
 void sync_self(afe_mesh* m) {
   afe::Batch& b = m->self;
+  b.ring_cap = m->sched.ring_cap;
+  b.narrow = m->sched.narrow;
+  b.order = m->sched.cost_order ? m->d_order : nullptr;
   b.nh = 1;
   b.Nmax = m->topo.Nmax;
   b.Smax = m->topo.Smax;
@@ -352,6 +358,59 @@ afe_status check_params(const afe_params* p) {
   if (p->kappa < 0.0 && !(p->Pr > 0.0)) return fail(AFE_EINVAL, "Pr > 0 is required when kappa < 0");
   return AFE_OK;
 }
+
+afe_status check_schedule(const afe_schedule* s) {
+  if (!s) return fail(AFE_EINVAL, "schedule is NULL");
+  if ((s->cost_order != 0 && s->cost_order != 1) || (s->variant != 0 && s->variant != 1) ||
+      (s->narrow != 0 && s->narrow != 1) || s->ring_cap < 0 || s->ring_cap > afe::kF32MaxStages)
+    return fail(AFE_EINVAL, "schedule: cost_order, variant and narrow are 0 or 1, ring_cap 0..8");
+  return AFE_OK;
+}
+
+// Estimated flops of one fixed-point iteration of a cell (the stiffness contraction and the
+// M_i^-1 apply dominate).
+double cell_cost(int N, int64_t Ni, int64_t S) {
+  const double Np = (N + 1) * (N + 2) * (N + 3) / 6, Nt = N + 1;
+  return (double)S * Nt * Np * (155.0 + 30.0 * Np) + 10.0 * Nt * (double)Ni * (double)Ni;
+}
+
+// Global cells of the given topologies (concatenated in order) sorted by decreasing cost;
+// equal costs keep index order.
+std::vector<int32_t> cost_order(const std::vector<const afe::Topology*>& tops, int N) {
+  std::vector<std::pair<double, int32_t>> v;
+  int64_t base = 0;
+  for (const afe::Topology* t : tops) {
+    for (int64_t c = 0; c < t->C; ++c)
+      v.push_back({cell_cost(N, t->node_ptr[c + 1] - t->node_ptr[c], t->sub_ptr[c + 1] - t->sub_ptr[c]),
+                   (int32_t)(base + c)});
+    base += t->C;
+  }
+  std::stable_sort(v.begin(), v.end(), [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+    return a.first > b.first;
+  });
+  std::vector<int32_t> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].second;
+  return out;
+}
+
+// Signature of a set of meshes for the autotuner's memory: order, and per mesh its cell count
+// and an FNV-1a hash of the cells' node and sub-tet counts.
+std::string mesh_signature(const std::vector<const afe::Topology*>& tops, int N) {
+  std::string sig = "N" + std::to_string(N);
+  for (const afe::Topology* t : tops) {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t c = 0; c < t->C; ++c) {
+      const uint64_t a = (uint64_t)(t->node_ptr[c + 1] - t->node_ptr[c]), b = (uint64_t)(t->sub_ptr[c + 1] - t->sub_ptr[c]);
+      h = (h ^ a) * 1099511628211ull;
+      h = (h ^ b) * 1099511628211ull;
+    }
+    sig += "|" + std::to_string(t->C) + ":" + std::to_string(h);
+  }
+  return sig;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::string, afe_schedule> g_tune_cache;
 
 }  // namespace
 
@@ -805,12 +864,37 @@ afe_status afe_plan_info(const afe_mesh* m, afe_plan* out) {
   return AFE_OK;
 }
 
+afe_status afe_set_schedule(afe_mesh* m, const afe_schedule* s) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  AFE_TRY(check_schedule(s));
+  if (s->variant == 1 && m->p.precision == AFE_FP32 && !(m->f32_ok && m->f32_tc_fits))
+    return fail(AFE_EINVAL, "the cells do not fit the tensor-memory plan of the FP32 predictor");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  if (s->cost_order && !m->d_order) {
+    const std::vector<int32_t> ord = cost_order({&m->topo}, m->p.order);
+    AFE_TRY(m->upload(&m->d_order, ord));
+  }
+  m->sched = *s;
+  m->variant = s->variant;
+  m->f32_tc = (m->f32_ok && m->f32_tc_fits && s->variant == 1) ? 1 : 0;
+  sync_self(m);
+  return AFE_OK;
+}
+
+afe_status afe_get_schedule(const afe_mesh* m, afe_schedule* s) {
+  if (!m || !s) return fail(AFE_EINVAL, "NULL argument");
+  *s = m->sched;
+  s->variant = m->variant;
+  return AFE_OK;
+}
+
 afe_status afe_set_predictor_variant(afe_mesh* m, int32_t variant) {
   if (!m) return fail(AFE_EINVAL, "NULL mesh");
   if (variant != 0 && variant != 1) return fail(AFE_EINVAL, "variant must be 0 (mma.sync) or 1 (tcgen05)");
   if (variant == 1 && m->p.precision == AFE_FP32 && !(m->f32_ok && m->f32_tc_fits))
     return fail(AFE_EINVAL, "the cells do not fit the tensor-memory plan of the FP32 predictor");
   m->variant = variant;
+  m->sched.variant = variant;
   m->f32_tc = (m->f32_ok && m->f32_tc_fits && variant == 1) ? 1 : 0;
   return AFE_OK;
 }
@@ -848,9 +932,13 @@ struct afe_batch {
   bool have_graph = false;
   int pending = 0;
   int64_t launches = 0, graph_launches = 0;
+  afe_schedule sched{};
+  int32_t* d_order = nullptr;
+  int tc_fits = 0;  // the members' cells fit the tensor-memory plan together
   ~afe_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    if (d_order) cudaFree(d_order);
     if (d_work) cudaFree(d_work);
     if (own_stream && st) cudaStreamDestroy(st);
   }
@@ -951,9 +1039,11 @@ afe_status afe_batch_create(afe_mesh* const* members, int n_members, void* cuda_
   P.diag = 0;
   P.f32_ok = 1;
   P.f32_smem = m0->f32_smem;
-  P.f32_tc = afe::tc_cell_plan(P.order, P.f32_smem, Smax, Nmax).ok ? 1 : 0;
+  b->tc_fits = afe::tc_cell_plan(P.order, P.f32_smem, Smax, Nmax).ok ? 1 : 0;
+  P.f32_tc = b->tc_fits;
   for (afe_mesh* m : b->mem)
     if (m->variant != 1) P.f32_tc = 0;
+  b->sched.variant = P.f32_tc;
   P.d_ref = m0->d_ref;
   P.single = nullptr;
   P.prof = nullptr;
@@ -1013,6 +1103,138 @@ afe_status afe_batch_sync(afe_batch* b, int* member_status) {
   b->pending = 0;
   if (worst != AFE_OK) return fail(worst, first_msg);
   return AFE_OK;
+}
+
+afe_status afe_batch_set_schedule(afe_batch* b, const afe_schedule* s) {
+  if (!b) return fail(AFE_EINVAL, "NULL batch");
+  AFE_TRY(check_schedule(s));
+  if (s->variant == 1 && !b->tc_fits)
+    return fail(AFE_EINVAL, "the members' cells do not fit the tensor-memory plan together");
+  AFE_CUDA(cudaStreamSynchronize(b->st));
+  if (s->cost_order && !b->d_order) {
+    std::vector<const afe::Topology*> tops;
+    for (afe_mesh* m : b->mem) tops.push_back(&m->topo);
+    const std::vector<int32_t> ord = cost_order(tops, b->plan.order);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, ord.size() * sizeof(int32_t));
+    if (e != cudaSuccess) return fail(AFE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    b->d_order = (int32_t*)p;
+    AFE_CUDA(cudaMemcpy(b->d_order, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
+  b->sched = *s;
+  b->bt.ring_cap = s->ring_cap;
+  b->bt.narrow = s->narrow;
+  b->bt.order = s->cost_order ? b->d_order : nullptr;
+  b->plan.f32_tc = s->variant;
+  b->have_graph = false;  // the captured graph holds the old table
+  return AFE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Times `trials` launches of the predictor alone for every candidate schedule (after computing
+// the time step of the current state) and sets the fastest.  `set` applies a schedule, `plan`
+// returns the launch plan under the schedule last applied.
+template <typename SetFn, typename PlanFn>
+afe_status autotune_impl(const std::string& sig, int order, bool tc_fits, int* work, cudaStream_t st, int trials,
+                         SetFn set, PlanFn plan, afe_schedule* best, double* best_ms, double* default_ms) {
+  if (trials < 1 || trials > 64) return fail(AFE_EINVAL, "trials must be in 1..64");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      AFE_TRY(set(it->second));
+      if (best) *best = it->second;
+      if (best_ms) *best_ms = -1.0;
+      if (default_ms) *default_ms = -1.0;
+      return AFE_OK;
+    }
+  }
+  {
+    const StepPlan P = plan();
+    afe::flags_clear_kernel<<<1, 64, 0, st>>>(*P.b);
+    afe::step_begin_kernel<<<1, 64, 0, st>>>(*P.b);
+    AFE_TRY(enqueue_dt(P, -1.0));
+  }
+  cudaEvent_t e0, e1;
+  AFE_CUDA(cudaEventCreate(&e0));
+  AFE_CUDA(cudaEventCreate(&e1));
+  std::vector<afe_schedule> cand;
+  for (int co = 0; co < 2; ++co)
+    for (int va = 0; va < (tc_fits ? 2 : 1); ++va)
+      for (int rc : {0, 2})
+        for (int na = 0; na < (afe::f32_ntp(order) == 4 ? 2 : 1); ++na) cand.push_back(afe_schedule{co, va, rc, na});
+  double tbest = 1e300, tdef = -1.0;
+  afe_schedule sbest = cand[0];
+  afe_status status = AFE_OK;
+  for (const afe_schedule& c : cand) {
+    status = set(c);
+    if (status != AFE_OK) break;
+    const StepPlan P = plan();
+    float ms = 0.f;
+    for (int r = 0; r <= trials && status == AFE_OK; ++r) {
+      if (r == 1) cudaEventRecord(e0, st);
+      cudaMemsetAsync(work, 0, sizeof(int), st);
+      status = stage(P, 0);
+    }
+    if (status != AFE_OK) break;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      status = fail(AFE_ECUDA, "autotune: event timing failed");
+      break;
+    }
+    const double t = ms / trials;
+    if (c.cost_order == 0 && c.variant == 0 && c.ring_cap == 0 && c.narrow == 0) tdef = t;
+    if (t < tbest) {
+      tbest = t;
+      sbest = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != AFE_OK) return status;
+  AFE_TRY(set(sbest));
+  {  // the tuning launches' status flags (iteration cap) are not a step's
+    const StepPlan P = plan();
+    afe::flags_clear_kernel<<<1, 64, 0, st>>>(*P.b);
+    AFE_CUDA(cudaStreamSynchronize(st));
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[sig] = sbest;
+  }
+  if (best) *best = sbest;
+  if (best_ms) *best_ms = tbest;
+  if (default_ms) *default_ms = tdef;
+  return AFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+afe_status afe_autotune(afe_mesh* m, int trials, afe_schedule* best, double* best_ms, double* default_ms) {
+  if (!m) return fail(AFE_EINVAL, "NULL mesh");
+  if (m->p.precision != AFE_FP32 || !m->f32_ok)
+    return fail(AFE_EINVAL, "autotune: the handle does not use the FP32 shared-memory predictor");
+  AFE_CUDA(cudaStreamSynchronize(m->stream));
+  return autotune_impl(
+      "mesh:" + mesh_signature({&m->topo}, m->p.order), m->p.order, m->f32_tc_fits != 0, m->dm.work, m->stream,
+      trials, [&](const afe_schedule& c) { return afe_set_schedule(m, &c); }, [&]() { return plan_of(m); }, best,
+      best_ms, default_ms);
+}
+
+afe_status afe_batch_autotune(afe_batch* b, int trials, afe_schedule* best, double* best_ms, double* default_ms) {
+  if (!b) return fail(AFE_EINVAL, "NULL batch");
+  AFE_CUDA(cudaStreamSynchronize(b->st));
+  std::vector<const afe::Topology*> tops;
+  for (afe_mesh* m : b->mem) tops.push_back(&m->topo);
+  return autotune_impl(
+      "batch:" + mesh_signature(tops, b->plan.order), b->plan.order, b->tc_fits != 0, b->d_work, b->st, trials,
+      [&](const afe_schedule& c) { return afe_batch_set_schedule(b, &c); }, [&]() { return b->plan; }, best, best_ms,
+      default_ms);
 }
 
 afe_status afe_batch_info(const afe_batch* b, int64_t* n_cells, int64_t* n_nodes, int64_t* launches,

@@ -84,8 +84,11 @@ constexpr int kMaxBatch = 64;
 struct Batch {
   int nh;                        // members in use
   int Nmax, Smax;                // maxima over the members (shared-memory layout)
+  int ring_cap;                  // FP32 predictor: most M_i^-1 ring stages (0: as many as fit)
+  int narrow;                    // FP32 predictor: 1 = narrow right-hand-side chunks everywhere
   int pad;
   int* work;                     // work counter of the persistent predictor
+  const int32_t* order;          // global cells in the order the predictor takes them (NULL: index order)
   int64_t cpre[kMaxBatch + 1];   // prefix sums of the members' cells
   int64_t gpre[kMaxBatch + 1];   // prefix sums of the members' polygonal faces
   DevMesh tab[kMaxBatch];

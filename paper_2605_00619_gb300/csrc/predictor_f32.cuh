@@ -507,7 +507,10 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   auto rec_a = [&](int k) { return reinterpret_cast<const uint16_t*>(srec + (size_t)k * REC + 40); };
 
   for (;;) {
-    if (tid == 0) sCell = atomicAdd(bt.work, 1);
+    if (tid == 0) {  // next cell of the work queue (index order, or the schedule's cost order)
+      const int w = atomicAdd(bt.work, 1);
+      sCell = (bt.order != nullptr && (int64_t)w < total) ? (int64_t)bt.order[w] : (int64_t)w;
+    }
     __syncthreads();
     const int64_t gc = sCell;
     if (gc >= total) break;
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     // the M_i^-1 ring takes as many stages as fit (the same plans the host reports)
     const F32CellPlan plan = f32_cell_plan(N, (size_t)smem_bytes, bt.Smax, Ni);
     const TcCellPlan tplan = tc_cell_plan(N, (size_t)smem_bytes, bt.Smax, Ni);
-    const bool wide = TC ? tplan.wide : plan.wide;
+    const bool wide = (TC ? tplan.wide : plan.wide) && !bt.narrow;
     const int CHc = wide ? 2 * CH : CH;
     float* sR = reinterpret_cast<float*>(shared_region);                          // phase 1, epilogue
     float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc][3 NP][5][NTP]
@@ -545,7 +548,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     float* ring = reinterpret_cast<float*>(shared_region + (TC ? f32_up128(tc_bop_bytes(N, Ni)) : 0));
     const int srows = TC ? tplan.rows : kF32Rows;  // rows of M_i^-1 per stage
     const int stage_floats = srows * LD;
-    const int nstage = TC ? tplan.nstage : plan.nstage;
+    const int nstage = min(TC ? tplan.nstage : plan.nstage, bt.ring_cap > 0 ? bt.ring_cap : kF32MaxStages);
     const int nblk = (Ni + srows - 1) / srows;
 
     // the cell's sub-tet records arrive by one bulk copy while the state is loaded

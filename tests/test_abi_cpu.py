@@ -120,7 +120,7 @@ def test_ctypes_structures_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     lines = []
-    for cls in (mod.afe_params, mod.afe_stats, mod.afe_plan):
+    for cls in (mod.afe_params, mod.afe_stats, mod.afe_plan, mod.afe_schedule):
         name = cls.__name__
         lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
         for field, _ in cls._fields_:
@@ -136,7 +136,7 @@ def test_ctypes_structures_match_the_header(tmp_path):
         if line:
             name, field, val = line.split()
             got[(name, field)] = int(val)
-    for cls in (mod.afe_params, mod.afe_stats, mod.afe_plan):
+    for cls in (mod.afe_params, mod.afe_stats, mod.afe_plan, mod.afe_schedule):
         name = cls.__name__
         assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:

@@ -279,3 +279,66 @@ def test_elastic_serving_results_equal_alone(afe, meshes):
     for h in solo.values():
         afe.afe_mesh_destroy(h)
     eng.close()
+
+
+@pytest.mark.parametrize("sched", [dict(cost_order=1), dict(narrow=1), dict(ring_cap=1), dict(cost_order=1, ring_cap=2)])
+def test_schedules_leave_every_member_unchanged(afe, meshes, sched):
+    """The predictor's schedule (cells in decreasing cost across the members, narrow chunks, a
+    shallower M_i^-1 ring) changes how work is laid out, not what is computed: every member
+    equals stepping it alone with the default schedule, bit for bit."""
+    mem = _members(afe, meshes)
+    ref = _alone(afe, mem, 3)
+    for h, u0 in mem:
+        afe.afe_set_state(h, u0)
+    b = afe.afe_batch_create([h for h, _ in mem])
+    afe.afe_batch_set_schedule(b, **sched)
+    afe.afe_batch_step_async(b, 0.0, 3, True)
+    _, ms = afe.afe_batch_sync(b, len(mem), check=False)
+    afe.afe_batch_destroy(b)
+    for i, ((h, _), (qa, _, sta)) in enumerate(zip(mem, ref)):
+        np.testing.assert_array_equal(afe.afe_get_state(h), qa, err_msg=f"member {i}")
+        assert ms[i] == sta
+    for h, _ in mem:
+        afe.afe_mesh_destroy(h)
+
+
+def test_autotuned_batch_and_mesh(afe, meshes):
+    """The autotuner times the candidate schedules, sets the fastest and remembers it per mesh
+    signature; the tuned batch's members match the default schedule's results (bit for bit
+    unless the tensor-memory form was chosen, then to FP32 rounding), and a tuned single
+    handle matches its untuned twin likewise."""
+    from tests.harness import rel_l2
+    mem = _members(afe, meshes)
+    ref = _alone(afe, mem, 3)
+    for h, u0 in mem:
+        afe.afe_set_state(h, u0)
+    b = afe.afe_batch_create([h for h, _ in mem])
+    sched, best, default = afe.afe_batch_autotune(b, 2)
+    assert best > 0 and default > 0 and best <= default * 1.0001
+    afe.afe_batch_step_async(b, 0.0, 3, True)
+    afe.afe_batch_sync(b, len(mem), check=False)
+    sched2, best2, _ = afe.afe_batch_autotune(b, 2)  # remembered: set, not timed again
+    assert best2 == -1.0 and (sched2.cost_order, sched2.variant, sched2.ring_cap, sched2.narrow) == \
+        (sched.cost_order, sched.variant, sched.ring_cap, sched.narrow)
+    afe.afe_batch_destroy(b)
+    for i, ((h, _), (qa, _, _)) in enumerate(zip(mem, ref)):
+        q = afe.afe_get_state(h)
+        if sched.variant == 0:
+            np.testing.assert_array_equal(q, qa, err_msg=f"member {i}")
+        else:
+            assert rel_l2(q, qa) <= 1e-6
+    h, u0 = mem[0]
+    afe.afe_set_state(h, u0)
+    s1, b1, d1 = afe.afe_autotune(h, 2)
+    assert b1 > 0 and afe.afe_get_schedule(h).cost_order == s1.cost_order
+    afe.afe_step_async(h, 0.0, 3)
+    afe.afe_sync(h, check=False)
+    q = afe.afe_get_state(h)
+    if s1.variant == 0:
+        np.testing.assert_array_equal(q, ref[0][0])
+    else:
+        assert rel_l2(q, ref[0][0]) <= 1e-6
+    with pytest.raises(afe.AfeError):
+        afe.afe_set_schedule(h, ring_cap=9)
+    for h, _ in mem:
+        afe.afe_mesh_destroy(h)
