@@ -65,6 +65,8 @@ def _args():
     ap.add_argument("--visc-dt", default="subtet", choices=["subtet", "cell"],
                     help="shock/tgv: length in the viscous term of the time step (the smallest "
                          "sub-tet length, or the cell length as printed; see the stokes study)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default predictor schedule instead of the autotuned one")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1],
                     help="FP32 predictor's M_i^-1 apply: 0 mma.sync, 1 tcgen05 with tensor memory")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
@@ -438,6 +440,7 @@ def ours(args):
         p = afe.afe_default_params(args.order, precision=prec, picard_tol=1e-6 if fp32 else 1e-12,
                                    picard_max=128 if fp32 else 64, cfl=cfl, **extra)
         h = afe.create_from_polymesh(pm, p, stream=sid)
+        tune = None
         if prec == afe.AFE_FP32:
             afe.afe_set_predictor_variant(h, args.variant)
         n_nodes = afe.afe_num_nodes(h)
@@ -450,6 +453,10 @@ def ours(args):
         else:
             u0 = states.density_wave(x)
         afe.afe_set_state(h, u0)
+        if fp32 and args.autotune:
+            sched, best_ms, default_ms = afe.afe_autotune(h, 3)
+            tune = {"cost_order": sched.cost_order, "variant": sched.variant, "ring_cap": sched.ring_cap,
+                    "narrow": sched.narrow, "predictor_ms": best_ms, "default_schedule_ms": default_ms}
         afe.afe_step_async(h, 0.0, warmup)
         st = afe.afe_sync(h, check=False)
         barrier()
@@ -478,7 +485,7 @@ def ours(args):
         _, iters, _, _ = afe.afe_get_diagnostics(h, pm.n_cells, qbar=False)
         rec = dict(status=[st, st2], ms=ms, wall=wall, stage_ms=(stage_ms / max(nst, 1)).tolist(), clocks=clk,
                    n_nodes=n_nodes, launches=launches, iters_mean=float(iters.mean()), iters_max=int(iters.max()),
-                   nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h))
+                   nonconverged=int(stats.nonconverged), dt=stats.dt, bytes=afe.afe_device_bytes(h), schedule=tune)
         rec["f_con"], rec["f_pw"], rec["abytes"], rec["abytes_streamed"] = predictor_model(
             node_ptr, pm.cell_subtet_ptr, iters, args.order, 4 if prec == afe.AFE_FP32 else 8)
         if e2e:
@@ -523,6 +530,7 @@ def ours(args):
         "status": {"fp32": r32["status"], "picard_iters_mean": r32["iters_mean"], "picard_iters_max": r32["iters_max"],
                    "nonconverged_cells": r32["nonconverged"]},
         "stage_ms_per_step": dict(zip(["limiter_dt", "predictor", "face", "corrector"], r32["stage_ms"])),
+        "predictor_schedule": r32["schedule"],
     }
     if "e2e_wall" in r32:
         e2e_wall = max_over_ranks(r32["e2e_wall"])
