@@ -114,24 +114,32 @@ def limiter(mesh: OracleMesh, u_cells, prm: Params):
     faces contribute nothing.
     """
     ub = cell_means(mesh, u_cells)
-    rho, v, p = primitives(ub, prm.gamma)
-    c = sound_speed(rho, p, prm.gamma)
     C = mesh.n_cells
     beta = np.zeros(C)
     mu_c = np.full(C, prm.mu)
-    for i, cd in enumerate(mesh.cells):
-        div = 0.0
-        cmin = c[i]
-        for bt in cd.bfaces:
-            if bt.nbr < 0:
-                continue
-            div += bt.area * float((v[bt.nbr] - v[i]) @ bt.normal)
-            cmin = min(cmin, c[bt.nbr])
-        div /= cd.vol
-        beta[i] = min(1.0, max(0.0, -(div + prm.m1 * cmin) / (prm.m1 * cmin)))
-        lam = np.linalg.norm(v[i]) + c[i]
-        mu_c[i] = prm.mu + beta[i] * rho[i] * lam * cell_length(cd, prm) / (2 * mesh.N + 1)
+    for i in range(C):
+        beta[i], mu_c[i] = limiter_cell(mesh, i, ub, prm)
     return beta, mu_c
+
+
+def limiter_cell(mesh: OracleMesh, i, ub, prm: Params):
+    """beta_i and mu_i of cell i from the cell means ``ub`` (indexable by cell: the cell's own
+    and its face neighbours' means are read)."""
+    rho, v, p = primitives(ub[i], prm.gamma)
+    c_i = sound_speed(rho, p, prm.gamma)
+    cd = mesh.cells[i]
+    div = 0.0
+    cmin = c_i
+    for bt in cd.bfaces:
+        if bt.nbr < 0:
+            continue
+        rn, vn, pn = primitives(ub[bt.nbr], prm.gamma)
+        div += bt.area * float((vn - v) @ bt.normal)
+        cmin = min(cmin, sound_speed(rn, pn, prm.gamma))
+    div /= cd.vol
+    beta = min(1.0, max(0.0, -(div + prm.m1 * cmin) / (prm.m1 * cmin)))
+    lam = np.linalg.norm(v) + c_i
+    return beta, prm.mu + beta * rho * lam * cell_length(cd, prm) / (2 * mesh.N + 1)
 
 
 # ---------------------------------------------------------------------------
@@ -146,16 +154,28 @@ def cell_length(cd, prm: Params) -> float:
 
 def cfl_dt(mesh: OracleMesh, u_cells, mu_c, prm: Params):
     """dt = CFL min h / ((2N+1) max(|lambda| + 2 |lambda^v| (2N+1)/h)) over all nodes at t^n."""
+    worst, h_min = cfl_pieces(mesh, u_cells, mu_c, prm, range(mesh.n_cells))
+    return cfl_from_pieces(mesh, worst, h_min, prm)
+
+
+def cfl_pieces(mesh: OracleMesh, u_cells, mu_c, prm: Params, cells):
+    """The two reductions of the CFL time step over ``cells``: the largest bracket
+    |lambda| + 2 |lambda^v| (2N+1)/h at their nodes, and the smallest characteristic length."""
     N = mesh.N
     worst = 0.0
-    for i, (cd, u) in enumerate(zip(mesh.cells, u_cells)):
+    for i in cells:
+        cd, u = mesh.cells[i], u_cells[i]
         rho, v, p = primitives(u, prm.gamma)
         lam = np.linalg.norm(v, axis=1) + sound_speed(rho, p, prm.gamma)
         lv = viscous_eigen(rho, mu_c[i], cell_kappa(mu_c[i], prm), prm)
         hv = cd.hsub if prm.visc_dt_subtet else cell_length(cd, prm)
         worst = max(worst, float(np.max(lam + 2.0 * lv * (2 * N + 1) / hv)))
-    h_min = min(cell_length(cd, prm) for cd in mesh.cells)
-    return prm.cfl * h_min / ((2 * N + 1) * worst)
+    h_min = min(cell_length(mesh.cells[i], prm) for i in cells)
+    return worst, h_min
+
+
+def cfl_from_pieces(mesh: OracleMesh, worst, h_min, prm: Params):
+    return prm.cfl * h_min / ((2 * mesh.N + 1) * worst)
 
 
 # ---------------------------------------------------------------------------
@@ -293,42 +313,54 @@ def step(mesh: OracleMesh, u_cells, prm: Params, dt=None, cells=None):
 
     new = [u.copy() for u in u_cells]
     for i in out_cells:
-        cd = mesh.cells[i]
         qbar_i, Fbar_i = pred[i]
-        vol = volume_term(mesh, i, Fbar_i)
-        # per-node states on both sides of every boundary sub-triangle
-        sides = []
-        for bt in cd.bfaces:
-            qm = qbar_i[bt.nodes]
-            Fm = Fbar_i[bt.k][bt.local]
-            if bt.nbr >= 0:
-                nb = mesh.cells[bt.nbr].bfaces[bt.nbr_tri]
-                qbar_j, Fbar_j = pred[bt.nbr]
-                qp = qbar_j[nb.nodes]
-                Fp = Fbar_j[nb.k][nb.local]
-                hp, mup, kp = cell_length(mesh.cells[bt.nbr], prm), mu_c[bt.nbr], kap[bt.nbr]
-            else:  # transmissive boundary: outer state = inner state
-                qp, Fp, hp, mup, kp = qm, Fm, cell_length(cd, prm), mu_c[i], kap[i]
-            sides.append((qm, Fm, qp, Fp, hp, mup, kp))
-        # wave speeds: max over all nodes of the polyhedral face, both sides (Eq. 3.33)
-        smax: dict = {}
-        vmax: dict = {}
-        for bt, (qm, Fm, qp, Fp, hp, mup, kp) in zip(cd.bfaces, sides):
-            sm = 0.0
-            sv = 0.0
-            for qq, mm, kk in ((qm / dt, mu_c[i], kap[i]), (qp / dt, mup, kp)):
-                rho, v, p = primitives(qq, prm.gamma)
-                sm = max(sm, float(np.max(np.abs(v @ bt.normal) + sound_speed(rho, p, prm.gamma))))
-                sv = max(sv, float(np.max(viscous_eigen(rho, mm, kk, prm))))
-            smax[bt.group] = max(smax.get(bt.group, 0.0), sm)
-            vmax[bt.group] = max(vmax.get(bt.group, 0.0), sv)
-        Gs = []
-        for bt, (qm, Fm, qp, Fp, hp, mup, kp) in zip(cd.bfaces, sides):
-            Gs.append(rusanov(qm, Fm, qp, Fp, bt.normal, smax[bt.group], vmax[bt.group], cell_length(cd, prm),
-                              hp, N))
-        face = face_term(mesh, i, Gs)
-        new[i] = u_cells[i] + cd.Minv @ (vol - face)
+
+        def outer(bt, i=i):
+            nb = mesh.cells[bt.nbr].bfaces[bt.nbr_tri]
+            qbar_j, Fbar_j = pred[bt.nbr]
+            return (qbar_j[nb.nodes], Fbar_j[nb.k][nb.local], cell_length(mesh.cells[bt.nbr], prm), mu_c[bt.nbr],
+                    kap[bt.nbr])
+
+        new[i] = corrector_cell(mesh, i, u_cells[i], qbar_i, Fbar_i, outer, dt, mu_c[i], kap[i], prm)
     return new, StepInfo(dt=dt, iterations=iters, beta=beta, mu=mu_c)
+
+
+def corrector_cell(mesh: OracleMesh, i, u_i, qbar_i, Fbar_i, outer, dt, mu_i, kap_i, prm: Params):
+    """u_i^{n+1} of cell i (Sec. 4.4): the volume term, Rusanov fluxes on every boundary
+    sub-triangle with the wave speeds maximised over each polygonal face and both sides, the
+    face term and the M_i^-1 update.  ``outer(bt)`` gives, for a sub-triangle with a
+    neighbour, the neighbour side's (q_bar at the face nodes, F_bar at them, h, mu, kappa) in
+    the sub-triangle's face-node order."""
+    cd = mesh.cells[i]
+    N = mesh.N
+    vol = volume_term(mesh, i, Fbar_i)
+    # per-node states on both sides of every boundary sub-triangle
+    sides = []
+    for bt in cd.bfaces:
+        qm = qbar_i[bt.nodes]
+        Fm = Fbar_i[bt.k][bt.local]
+        if bt.nbr >= 0:
+            qp, Fp, hp, mup, kp = outer(bt)
+        else:  # transmissive boundary: outer state = inner state
+            qp, Fp, hp, mup, kp = qm, Fm, cell_length(cd, prm), mu_i, kap_i
+        sides.append((qm, Fm, qp, Fp, hp, mup, kp))
+    # wave speeds: max over all nodes of the polyhedral face, both sides (Eq. 3.33)
+    smax: dict = {}
+    vmax: dict = {}
+    for bt, (qm, Fm, qp, Fp, hp, mup, kp) in zip(cd.bfaces, sides):
+        sm = 0.0
+        sv = 0.0
+        for qq, mm, kk in ((qm / dt, mu_i, kap_i), (qp / dt, mup, kp)):
+            rho, v, p = primitives(qq, prm.gamma)
+            sm = max(sm, float(np.max(np.abs(v @ bt.normal) + sound_speed(rho, p, prm.gamma))))
+            sv = max(sv, float(np.max(viscous_eigen(rho, mm, kk, prm))))
+        smax[bt.group] = max(smax.get(bt.group, 0.0), sm)
+        vmax[bt.group] = max(vmax.get(bt.group, 0.0), sv)
+    Gs = []
+    for bt, (qm, Fm, qp, Fp, hp, mup, kp) in zip(cd.bfaces, sides):
+        Gs.append(rusanov(qm, Fm, qp, Fp, bt.normal, smax[bt.group], vmax[bt.group], cell_length(cd, prm), hp, N))
+    face = face_term(mesh, i, Gs)
+    return u_i + cd.Minv @ (vol - face)
 
 
 def conserved_totals(mesh: OracleMesh, u_cells):
