@@ -70,7 +70,8 @@ def _args():
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1],
                     help="FP32 predictor's M_i^-1 apply: 0 mma.sync, 1 tcgen05 with tensor memory")
     ap.add_argument("--serve", action="store_true", help="serving run: Poisson requests on small meshes")
-    ap.add_argument("--study", choices=["convergence", "stokes", "vortex", "shock"], help="accuracy study instead of the throughput run")
+    ap.add_argument("--study", choices=["convergence", "stokes", "vortex", "shock", "tgv"],
+                    help="accuracy study instead of the throughput run")
     ap.add_argument("--workload", default="density", choices=["density", "shock", "tgv"],
                     help="density: density wave, periodic unit cube, Euler; shock: spherical explosion on "
                          "[-1,1]^3, transmissive, limiter on; tgv: Navier-Stokes Taylor-Green vortex on "
@@ -905,6 +906,70 @@ def shock_study(args):
                       **cmp, "reference": "radial MUSCL, Rusanov flux, 15000 cells on r in [0, 1.75]"}), flush=True)
 
 
+def tgv_study(args):
+    """The compressible Navier-Stokes Taylor-Green vortex (the fourth configuration of the
+    method's evaluation: mu 0.01, Pr 0.71, kappa from Pr, p0 100) on the periodic [0, 2pi)^3
+    mesh of ``--n``^3 cells at order ``--order``, FP32 form, CFL steps of ``--cfl`` (default
+    the stable CFL) to t = 1, viscous time step from the sub-tet length unless ``--visc-dt
+    cell``.  Reported: the status, the time reached, steps, ms per step and the kinetic energy
+    (volume-weighted nodal sum of rho |v|^2 / 2) every 0.1 time units; a run that ends
+    non-finite reports where.
+    """
+    import numpy as np
+    import torch
+
+    from inputs import states
+    from inputs.voronoi import periodic_voronoi
+    from paper_2605_00619_gb300 import afe
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    afe.lib()
+    t_end, N, n = 1.0, args.order, args.n
+    cfl = args.cfl if args.cfl is not None else STABLE_CFL[N]
+    pm = periodic_voronoi(n, L=2 * math.pi)
+    sub = pm.subtet_coords()
+    vol = np.bincount(np.repeat(np.arange(pm.n_cells), np.diff(pm.cell_subtet_ptr)),
+                      weights=np.abs(np.linalg.det(sub[:, 1:] - sub[:, :1])) / 6.0, minlength=pm.n_cells)
+    p = afe.afe_default_params(N, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128, cfl=cfl,
+                               equations=afe.AFE_NAVIER_STOKES, mu=0.01, Pr=0.71, kappa=-1.0,
+                               visc_dt_subtet=int(args.visc_dt == "subtet"))
+    h = afe.create_from_polymesh(pm, p)
+    x = afe.afe_get_node_coords(h)
+    ptr = afe.afe_node_ptr(h, pm.n_cells)
+    wn = np.repeat(vol / np.diff(ptr), np.diff(ptr))
+
+    def kinetic(q):
+        return float(np.sum(wn * 0.5 * (q[:, 1] ** 2 + q[:, 2] ** 2 + q[:, 3] ** 2) / q[:, 0]))
+
+    afe.afe_set_state(h, states.taylor_green_3d(x, p0=100.0))
+    history = [(0.0, kinetic(afe.afe_get_state(h)))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    status, steps, t_mark = 0, 0, 0.1
+    while True:
+        s = afe.afe_get_stats(h)
+        if s.t >= t_end - 1e-12:
+            break
+        k = 1 if steps == 0 else max(1, min(50, int((t_mark - s.t) / max(s.dt, 1e-30))))
+        afe.afe_step_async(h, 0.0, k)
+        st = afe.afe_sync(h, check=False)
+        steps += k
+        if st not in (0, afe.AFE_ENOCONV):
+            status = st
+            break
+        t = afe.afe_get_stats(h).t
+        if t >= t_mark - 1e-12:
+            history.append((t, kinetic(afe.afe_get_state(h))))
+            t_mark += 0.1
+    wall = time.perf_counter() - t0
+    s = afe.afe_get_stats(h)
+    afe.afe_mesh_destroy(h)
+    print(json.dumps({"study": "tgv", "workload": workload_name(n, N, "tgv") + ", to t = 1, FP32", "cfl": cfl,
+                      "visc_dt": args.visc_dt, "status": int(status), "t": s.t, "steps": steps,
+                      "ms_per_step": 1e3 * wall / max(steps, 1), "kinetic_energy": history,
+                      "cells": pm.n_cells}), flush=True)
+
+
 def compare_with_radial(x, q, ptr, vol, rref, wref, r_max=0.95, ambient=0.125, gamma=1.4):
     """Nodal state q [n_nodes, 5] at positions x against a radial profile (rref, wref = rho, u,
     p): volume-weighted nodal L1 errors of rho, |u| and p over the nodes with r < r_max (each
@@ -1011,6 +1076,9 @@ def main():
         return
     if args.study == "shock":
         shock_study(args)
+        return
+    if args.study == "tgv":
+        tgv_study(args)
         return
     if args.serve:
         serve(args)
