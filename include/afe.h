@@ -265,6 +265,16 @@ afe_status afe_get_schedule(const afe_mesh* m, afe_schedule* s);
  * AFE_EINVAL); trials in 1..64. */
 afe_status afe_autotune(afe_mesh* m, int trials, afe_schedule* best, double* best_ms, double* default_ms);
 
+/* The two reductions of the CFL time step (Sec. 4.2) over the first `n_cells` cells of the
+ * handle, for stepping one mesh partitioned over several handles (ranks) with one global time
+ * step: with the limiter's viscosity of the current state (Sec. 4.5), *bracket_max receives the
+ * largest |lambda| + 2 |lambda^v| (2N+1)/h over the nodes of those cells and *h_min their
+ * smallest characteristic length.  The caller combines them over the ranks (max, min) and
+ * steps every rank with dt = cfl * h_min / ((2N+1) * bracket_max), the expression the library
+ * evaluates itself for a single mesh.  Synchronises the handle's stream; 1 <= n_cells <= the
+ * handle's cells, else AFE_EINVAL; an inadmissible state returns AFE_ENONFINITE. */
+afe_status afe_cfl_pieces(afe_mesh* m, int64_t n_cells, double* bracket_max, double* h_min);
+
 /* Conserved totals of a caller-provided device state, with no device memory allocated by the
  * call.  The paper has no counterpart: this serves callers that must not call cudaMalloc at
  * the point of use, e.g. code running inside a framework whose caching allocator owns all

@@ -122,6 +122,7 @@ _SIGS = {
     "afe_conserved_totals_noalloc": (ctypes.c_int, [_P, _P, _P, _P]),
     "afe_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(afe_plan)]),
     "afe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "afe_cfl_pieces": (ctypes.c_int, [_P, ctypes.c_int64, _D, _D]),
     "afe_set_predictor_variant": (ctypes.c_int, [_P, ctypes.c_int32]),
     "afe_set_schedule": (ctypes.c_int, [_P, ctypes.POINTER(afe_schedule)]),
     "afe_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(afe_schedule)]),
@@ -364,6 +365,13 @@ def afe_batch_autotune(b, trials: int = 3):
     x, d = ctypes.c_double(), ctypes.c_double()
     _check(lib().afe_batch_autotune(b, int(trials), ctypes.byref(s), ctypes.byref(x), ctypes.byref(d)))
     return s, x.value, d.value
+
+
+def afe_cfl_pieces(m, n_cells: int):
+    """(largest CFL bracket, smallest characteristic length) over the first n_cells cells."""
+    b, h = ctypes.c_double(), ctypes.c_double()
+    _check(lib().afe_cfl_pieces(m, int(n_cells), ctypes.byref(b), ctypes.byref(h)))
+    return b.value, h.value
 
 
 def afe_set_wait_limit(m, polls: int):

@@ -703,6 +703,33 @@ afe_status afe_compute_dt(afe_mesh* m, double* dt) {
   return status_of(flags);
 }
 
+afe_status afe_cfl_pieces(afe_mesh* m, int64_t n_cells, double* bracket_max, double* h_min) {
+  if (!m || !bracket_max || !h_min) return fail(AFE_EINVAL, "NULL argument");
+  if (n_cells < 1 || n_cells > m->topo.C) return fail(AFE_EINVAL, "n_cells must be in 1..cells of the handle");
+  const StepPlan P = plan_of(m);
+  afe::flags_clear_kernel<<<1, 64, 0, P.st>>>(*P.b);
+  afe::step_begin_kernel<<<1, 64, 0, P.st>>>(*P.b);
+  if (P.limiter) {  // the viscosity of every cell of the handle
+    const int64_t C = m->topo.C;
+    afe::cell_means_kernel<<<(int)std::min<int64_t>(C, (int64_t)P.n_sm * 8), 256, 0, P.st>>>(*P.b);
+    afe::limiter_kernel<<<(int)((C + 127) / 128), 128, 0, P.st>>>(*P.b);
+  }
+  afe::Batch sub = m->self;  // the bracket over the first n_cells cells only
+  sub.cpre[1] = n_cells;
+  afe::cfl_kernel<<<(int)((n_cells * 32 + 255) / 256), 256, 0, P.st>>>(sub);
+  AFE_CUDA(cudaGetLastError());
+  unsigned long long bits = 0;
+  AFE_CUDA(cudaMemcpyAsync(&bits, m->dm.maxbits, sizeof(bits), cudaMemcpyDeviceToHost, m->stream));
+  int flags[afe::F_COUNT];
+  AFE_TRY(read_flags(m, flags));
+  double bm;
+  std::memcpy(&bm, &bits, sizeof(bm));
+  *bracket_max = bm;
+  const std::vector<double>& hc = m->p.h_diameter ? m->topo.cell_diam : m->topo.cell_h;
+  *h_min = *std::min_element(hc.begin(), hc.begin() + n_cells);
+  return status_of(flags);
+}
+
 afe_status afe_step(afe_mesh* m, double dt) {
   if (!m) return fail(AFE_EINVAL, "NULL mesh");
   afe::flags_clear_kernel<<<1, 64, 0, m->stream>>>(m->self);

@@ -158,3 +158,23 @@ def test_two_rank_partitioned_step_equals_one_rank_oracle(case, world):
     res.sort()
     assert all(same for _, same, _, _ in res), res
     assert sum(n for _, _, n, _ in res) == 27 and all(h > 0 for _, _, _, h in res)
+
+
+@pytest.mark.parametrize("layers", [1, 2])
+def test_ghost_layers_and_send_lists(layers):
+    """The ghost layers of every rank and the send lists its peers derive from the same rule
+    agree: what rank s holds as ghosts from rank r is what r sends to s."""
+    pm = periodic_voronoi(4)
+    labels = P.bisect(P.cell_centroids(pm), 3)
+    nb = P.cell_neighbours(pm)
+    ghosts = {r: P.ghost_cells(nb, labels, r, layers) for r in range(3)}
+    for r in range(3):
+        own = set(np.flatnonzero(labels == r).tolist())
+        g = ghosts[r]
+        assert not (own & set(g)) and len(g) == len(set(g))
+        # layer 1 is exactly the off-rank face neighbours of the own cells
+        layer1 = {j for c in own for j in nb[c]} - own
+        assert layer1 <= set(g)
+        if layers == 1:
+            assert set(g) == layer1
+    assert all(len(v) > 0 for v in nb)
