@@ -56,7 +56,9 @@ typedef enum { AFE_FP64 = 0, AFE_FP32 = 1 } afe_precision;
 typedef enum { AFE_BC_PERIODIC = 0, AFE_BC_TRANSMISSIVE = 1 } afe_bc;
 
 typedef struct {
-  int order;          /* polynomial degree N in {1, 2, 3} (Sec. 4.1)                           */
+  int order;          /* polynomial degree N in {1, 2, 3, 4} (Sec. 4.1, App. A); at N = 4 the
+                         cells (about 1,100 nodes) exceed the FP32 shared-memory predictor and
+                         both forms run the global-scratch kernels                            */
   int equations;      /* afe_equations; Euler ignores mu, Pr, kappa unless the limiter adds mu */
   int precision;      /* afe_precision                                                         */
   double gamma;       /* ratio of specific heats (Sec. 2)                                      */

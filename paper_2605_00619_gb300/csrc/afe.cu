@@ -148,14 +148,16 @@ bool corrector_f32_fits(int Nmax) { return Nmax <= 2 * 4 * afe::kCorrThreads; }
 
 template <int N, typename Real>
 void launch_predictor(const StepPlan& P) {
-  if (sizeof(Real) == 4 && P.f32_ok) {
-    if (P.f32_tc)
-      afe::predictor_f32_kernel<N, true><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
-                                                                                       (int)P.f32_smem);
-    else
-      afe::predictor_f32_kernel<N, false><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
-                                                                                        (int)P.f32_smem);
-    return;
+  if constexpr (N <= 3) {  // the shared-memory FP32 predictor exists for N <= 3 (cells up to 640 nodes)
+    if (sizeof(Real) == 4 && P.f32_ok) {
+      if (P.f32_tc)
+        afe::predictor_f32_kernel<N, true><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
+                                                                                         (int)P.f32_smem);
+      else
+        afe::predictor_f32_kernel<N, false><<<P.n_sm, afe::kF32Threads, P.f32_smem, P.st>>>(*P.b, P.d_ref, P.diag,
+                                                                                          (int)P.f32_smem);
+      return;
+    }
   }
   afe_mesh* m = P.single;
   afe::predictor_kernel<N, Real><<<m->pred_grid, 256, 0, P.st>>>(m->dm, m->d_ref, (Real*)m->scratch,
@@ -237,8 +239,13 @@ afe_status dispatch_stage(const StepPlan& P, int stage) {
       else if (stage == 1) launch_face<3, Real>(P);
       else return launch_corrector<3, Real>(P);
       break;
+    case 4:
+      if (stage == 0) launch_predictor<4, Real>(P);
+      else if (stage == 1) launch_face<4, Real>(P);
+      else return launch_corrector<4, Real>(P);
+      break;
     default:
-      return fail(AFE_EINVAL, "order must be 1, 2 or 3");
+      return fail(AFE_EINVAL, "order must be 1, 2, 3 or 4");
   }
   return AFE_OK;
 }
@@ -347,7 +354,7 @@ void sync_self(afe_mesh* m) {
 
 afe_status check_params(const afe_params* p) {
   if (!p) return fail(AFE_EINVAL, "params is NULL");
-  if (p->order < 1 || p->order > 3) return fail(AFE_EINVAL, "order must be 1, 2 or 3");
+  if (p->order < 1 || p->order > 4) return fail(AFE_EINVAL, "order must be 1, 2, 3 or 4");
   if (p->precision != AFE_FP64 && p->precision != AFE_FP32) return fail(AFE_EINVAL, "unknown precision");
   if (p->equations != AFE_EULER && p->equations != AFE_NAVIER_STOKES) return fail(AFE_EINVAL, "unknown equations");
   if (!(p->gamma > 1.0) || !(p->R > 0.0) || !(p->cfl > 0.0) || !(p->picard_tol > 0.0) || p->picard_max < 1)
@@ -435,7 +442,7 @@ afe_status afe_default_params(afe_params* p, int order) {
   p->picard_tol = 1e-12;
   p->picard_max = 64;
   p->period[0] = p->period[1] = p->period[2] = 1.0;
-  return (order >= 1 && order <= 3) ? AFE_OK : fail(AFE_EINVAL, "order must be 1, 2 or 3");
+  return (order >= 1 && order <= 4) ? AFE_OK : fail(AFE_EINVAL, "order must be 1, 2, 3 or 4");
 }
 
 afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double* xyz, int64_t n_cells,
@@ -571,11 +578,13 @@ afe_status afe_mesh_create(const afe_params* p, int64_t n_vertices, const double
         afe::sub32_kernel<2><<<blocks, 256, 0, M->stream>>>(d, T.T);
         AFE_TRY(plan_f32<2>(M));
         break;
-      default:
+      case 3:
         AFE_TRY(M->alloc(&d.sub32, (size_t)T.T * afe::f32_rec_bytes(3)));
         afe::sub32_kernel<3><<<blocks, 256, 0, M->stream>>>(d, T.T);
         AFE_TRY(plan_f32<3>(M));
         break;
+      default:  // N = 4: the cells (about 1,100 nodes) exceed the shared-memory plan: the
+        break;  // global-scratch FP32 kernels run, which need no packed records
     }
   }
   // predictor scratch (persistent grid, one slice per block)

@@ -508,8 +508,12 @@ template <int N, typename Real>
 __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData* __restrict__ ref, Real* scratch,
                                                         int64_t scratch_stride, int diag) {
   constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N);
+  // the nodal derivative matrices stay in global memory (L1-cached) when both reference
+  // matrices would not fit the static shared-memory limit (FP64 at N = 4)
+  constexpr bool kDShared = 2 * 3 * NP * NP * sizeof(Real) <= 44 * 1024;
+  constexpr int DS = kDShared ? NP : 1;
   __shared__ Real sS[3][NP][NP];
-  __shared__ Real sD[3][NP][NP];
+  __shared__ Real sD[3][DS][DS];
   __shared__ Real sK[NT][NT];
   __shared__ Real sW[NT];
   __shared__ double sred[64];
@@ -518,8 +522,12 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
   for (int e = tid; e < 3 * NP * NP; e += nthr) {
     const int d = e / (NP * NP), r = (e / NP) % NP, q = e % NP;
     sS[d][r][q] = (Real)ref->S[d][r][q];
-    sD[d][r][q] = (Real)ref->D[d][r][q];
+    if constexpr (kDShared) sD[d][r % DS][q % DS] = (Real)ref->D[d][r][q];
   }
+  auto Dv = [&](int d, int j, int l) -> Real {
+    if constexpr (kDShared) return sD[d][j % DS][l % DS];
+    else return (Real)ref->D[d][j][l];
+  };
   if (tid < NT * NT) sK[tid / NT][tid % NT] = (Real)ref->K1tinv[tid / NT][tid % NT];
   if (tid < NT) sW[tid] = (Real)ref->w[tid];
   const int Nmax = m.Nmax, Smax = m.Smax;
@@ -575,7 +583,7 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
           const Real* ql = q + (Ak[l] * NT + t) * 5;
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const Real dd = sD[d][j][l];
+            const Real dd = Dv(d, j, l);
 #pragma unroll
             for (int v = 0; v < 5; ++v) gx[d][v] += dd * ql[v];
           }
@@ -632,7 +640,7 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
         Real acc = 0;
         for (int64_t p = m.inc_ptr[n0 + n]; p < m.inc_ptr[n0 + n + 1]; ++p) {
           const uint32_t w = m.inc[p];
-          const int k = (int)(w >> 5), j = (int)(w & 31);
+          const int k = (int)(w >> 6), j = (int)(w & 63);
           acc += Rb[((int64_t)(k * NT + t) * NP + j) * 5 + v];
         }
         RHS[e] = acc;
@@ -716,7 +724,7 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
       Real acc = 0;
       for (int64_t p = m.inc_ptr[n0 + n]; p < m.inc_ptr[n0 + n + 1]; ++p) {
         const uint32_t w = m.inc[p];
-        acc += Rb[((int64_t)(w >> 5) * NP + (w & 31)) * 5 + v];
+        acc += Rb[((int64_t)(w >> 6) * NP + (w & 63)) * 5 + v];
       }
       vol[(n0 + n) * 5 + v] = acc;
     }
@@ -753,7 +761,7 @@ __global__ void __launch_bounds__(256) predictor_kernel(DevMesh m, const RefData
             const Real* ql = q + (Ak[l] * NT + t) * 5;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-              const Real dd = sD[d][j][l];
+              const Real dd = Dv(d, j, l);
 #pragma unroll
               for (int v = 0; v < 5; ++v) gx[d][v] += dd * ql[v];
             }

@@ -127,9 +127,9 @@ __device__ __forceinline__ void gather_in_order(const uint32_t* __restrict__ inc
     for (int q = 0; q < 4; ++q) {
       ok[q] = cur + q < end;
       const uint32_t w = ok[q] ? inc[cur + q] : 0u;
-      const int k = (int)(w >> 5) - kc;
+      const int k = (int)(w >> 6) - kc;
       ok[q] = ok[q] && k < nk;  // a prefix of the four (the list is sorted by k)
-      src[q] = row_of(ok[q] ? k : 0, (int)(w & 31));
+      src[q] = row_of(ok[q] ? k : 0, (int)(w & 63));
     }
     float val[4][5];
 #pragma unroll
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   unsigned char* p = smem_raw;
   unsigned char* srec = p;  // [S][REC] sub-tet records of the current cell
   p += f32_up128((size_t)bt.Smax * REC);
-  uint32_t* sinc = reinterpret_cast<uint32_t*>(p);  // [incidences] (k << 5) | j of the cell's nodes
+  uint32_t* sinc = reinterpret_cast<uint32_t*>(p);  // [incidences] (k << 6) | j of the cell's nodes
   int* sincp = reinterpret_cast<int*>(p + f32_up128((size_t)bt.Smax * NP * 4));  // [N_i + 1] row offsets
   p += f32_inc_bytes(N, bt.Smax);
   unsigned char* const cell_base = p;  // per cell: sq, srhs, then {sR, sB | M_i^-1 ring}

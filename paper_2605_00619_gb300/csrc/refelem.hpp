@@ -1,4 +1,4 @@
-// Universal (mesh-independent) matrices of the AFE scheme for degree N = 1..3.
+// Universal (mesh-independent) matrices of the AFE scheme for degree N = 1..4.
 //
 // Reference tetrahedron {(r,s,t) >= 0, r+s+t <= 1} with the equispaced P_N node lattice
 // of App. A; Lagrange basis from the nodal property phi_j(x_m) = delta_jm (Sec. 4.1);
@@ -9,10 +9,10 @@
 
 namespace afe {
 
-constexpr int kMaxN = 3;
-constexpr int kMaxNp = 20;  // (N+1)(N+2)(N+3)/6 at N = 3
-constexpr int kMaxNt = 4;   // N+1
-constexpr int kMaxNf = 10;  // (N+1)(N+2)/2
+constexpr int kMaxN = 4;
+constexpr int kMaxNp = 35;  // (N+1)(N+2)(N+3)/6 at N = 4
+constexpr int kMaxNt = 5;   // N+1
+constexpr int kMaxNf = 15;  // (N+1)(N+2)/2
 
 struct RefData {
   int N, Np, Nt, Nf;
@@ -29,7 +29,7 @@ struct RefData {
   double K1tinv[kMaxNt][kMaxNt];
 };
 
-// Fills `out` for degree N (1..3); returns false on an unsupported N.
+// Fills `out` for degree N (1..4); returns false on an unsupported N.
 bool build_ref(int N, RefData* out);
 
 // Index of the node with multi-index a[4], or -1.

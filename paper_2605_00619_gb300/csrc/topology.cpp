@@ -68,14 +68,15 @@ struct CellOut {
 };
 
 inline uint64_t pack_node(int n, const int* lv, const int* al) {
-  // sorted (local vertex, weight) pairs with weight > 0: 12-bit vertex, 2-bit weight, plus the count
+  // sorted (local vertex, weight) pairs with weight > 0: 12-bit vertex, 3-bit weight (N <= 4),
+  // after the count in the low 4 bits
   int idx[4], m = 0;
   for (int k = 0; k < n; ++k)
     if (al[k] > 0) idx[m++] = k;
   for (int a = 1; a < m; ++a)
     for (int b = a; b > 0 && lv[idx[b]] < lv[idx[b - 1]]; --b) std::swap(idx[b], idx[b - 1]);
   uint64_t key = (uint64_t)m;
-  for (int k = 0; k < m; ++k) key |= (uint64_t)(((lv[idx[k]] & 0xfff) << 2) | (al[idx[k]] & 3)) << (4 + 14 * k);
+  for (int k = 0; k < m; ++k) key |= (uint64_t)(((lv[idx[k]] & 0xfff) << 3) | (al[idx[k]] & 7)) << (4 + 15 * k);
   return key;
 }
 
@@ -233,7 +234,7 @@ void process_cell(const RefData& R, const double* xyz, const int64_t* vtx, const
   {
     std::vector<int> fill(off.begin(), off.end() - 1);
     for (int k = 0; k < S; ++k)
-      for (int j = 0; j < Np; ++j) out->inc[fill[out->A[(size_t)k * Np + j]]++] = ((uint32_t)k << 5) | (uint32_t)j;
+      for (int j = 0; j < Np; ++j) out->inc[fill[out->A[(size_t)k * Np + j]]++] = ((uint32_t)k << 6) | (uint32_t)j;
   }
 
   // triangles of the subgrid: interior ones appear twice, cell-boundary ones once

@@ -35,11 +35,12 @@ def test_library_exports_every_declared_symbol(afe):
 def test_default_params(afe):
     p = afe.afe_default_params(2)
     assert p.order == 2 and p.gamma == 1.4 and p.R == 1.0 and p.cfl == 0.3 and p.picard_tol == 1e-12
+    assert afe.afe_default_params(4).order == 4
     with pytest.raises(afe.AfeError):
         afe.afe_default_params(5)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_validate_counts_match_oracle(afe, N):
     for pm in (periodic_voronoi(2), box_voronoi(2)):
         p = afe.afe_default_params(N, period=pm.period if pm.periodic else (1, 1, 1))

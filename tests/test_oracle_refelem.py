@@ -86,7 +86,7 @@ def test_p4_lattice_counts():
     assert (kinds[3], kinds[2], kinds[1], kinds[0]) == (4, 18, 12, 1)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_nodal_property_and_partition_of_unity(N):
     R = ref_element(N)
     for j, p in enumerate(R.phi):
@@ -142,7 +142,7 @@ def test_universal_matrices_closed_forms(N):
                 assert R.Z_exact[a][b] == Fraction(1 + (a == b), 24)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_universal_matrices_against_quadrature(N):
     R = ref_element(N)
     xq, wq = _tet_quadrature(N + 4)
@@ -164,7 +164,7 @@ def test_universal_matrices_against_quadrature(N):
     np.testing.assert_allclose(R.Z[np.ix_(idx, idx)], Zq, atol=1e-15)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_integration_by_parts_pins_stiffness_to_face_mass(N):
     """S^_d + S^_d^T = sum over the four faces of n_d * (2 area) * Z^ on that face."""
     R = ref_element(N)
@@ -180,7 +180,7 @@ def test_integration_by_parts_pins_stiffness_to_face_mass(N):
     np.testing.assert_allclose(R.S + np.transpose(R.S, (0, 2, 1)), rhs, atol=1e-15)
 
 
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_time_basis(N):
     R = ref_element(N)
     assert abs(R.w.sum() - 1) < 1e-15

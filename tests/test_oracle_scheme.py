@@ -71,7 +71,7 @@ def _cell_quadrature(pm, i, n=6):
 
 
 @pytest.mark.parametrize("kind,n", [("per", 2), ("box", 2)])
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
 def test_mass_matrix_invariants(kind, n, N):
     pm, m = mesh(kind, n, N)
     tot = 0.0
@@ -613,3 +613,19 @@ def test_heat_conduction_and_longitudinal_viscosity_closed_forms():
     om = math.sqrt(k * k - 0.25 * b * b)
     closed = math.exp(-0.5 * b * T) * (math.cos(om * T) - 0.5 * b / om * math.sin(om * T))
     assert ratio == pytest.approx(closed, abs=3e-3)
+
+
+def test_p4_step_free_stream_and_conservation():
+    """N = 4 (App. A.4's quartic element): a constant state stays constant to round-off and a
+    density wave keeps the conserved totals, over one step on the periodic 2^3 mesh."""
+    pm, m = mesh("per", 2, 4)
+    x = m.node_coords()
+    u = states.constant(x)
+    new, info = scheme.step(m, m.split(u), scheme.Params())
+    assert np.abs(np.concatenate(new) - u).max() < 1e-12
+    u = states.density_wave(x)
+    t0 = scheme.conserved_totals(m, m.split(u))
+    new, info = scheme.step(m, m.split(u), scheme.Params())
+    t1 = scheme.conserved_totals(m, new)
+    assert np.abs(t1 - t0).max() <= 1e-13 * np.abs(t0).max()
+    assert info.iterations.max() < 64

@@ -246,3 +246,24 @@ def test_explosion_fp64_prefix_of_ten_steps(afe):
         assert pr.lib_step(check=False) in (0, 5)
     assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
     pr.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_p4_against_the_oracle(afe, prec):
+    """N = 4 (about 1,100 nodes per cell): both forms on the global-scratch kernels (the cells
+    exceed the shared-memory plan), 2 CFL steps of the density wave on the periodic 2^3 mesh;
+    FP64 to 1e-11 (L-infinity), FP32 to 1e-5 (L2)."""
+    pm = periodic_voronoi(2)
+    p = afe.afe_default_params(4) if prec == 0 else afe.afe_default_params(
+        4, precision=afe.AFE_FP32, picard_tol=1e-6, picard_max=128)
+    pr = Pair(pm, p)
+    assert afe.afe_plan_info(pr.h).fp32_shared == 0
+    pr.set_state(states.density_wave(pr.om.node_coords()))
+    for _ in range(2):
+        info = pr.oracle_step()
+        assert pr.lib_step(info.dt) == 0
+    if prec == 0:
+        assert rel_linf(pr.lib_state(), pr.u) <= FP64_TOL
+    else:
+        assert rel_l2(pr.lib_state(), pr.u) <= FP32_TOL
+    pr.close()
