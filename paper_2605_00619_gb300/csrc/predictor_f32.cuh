@@ -408,6 +408,180 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
     for (int v = 0; v < 5; ++v) out[d][v] = scale * (g[d * 3 + 0] * F[0][v] + g[d * 3 + 1] * F[1][v] + g[d * 3 + 2] * F[2][v]);
 }
 
+// Inputs of the tensor-memory apply's streaming loops (one cell-iteration).
+struct TcStreamArgs {
+  int warp, lane, Ni, LD, srows, stage_floats, nstage, nblk, SL, spr, nsl, ntl, nbuf;
+  float* ring;
+  const float* minv;
+  uint32_t tmem, bsh, sbo;
+  uint64_t *sfull, *sempty, *safull, *saempty, *sdfull;
+  int* abortp;
+  int* flags;
+};
+// Barrier parities and counts the streaming loops carry from one cell-iteration to the next.
+struct TcStreamState {
+  uint32_t fpar, epar, ipar, issued, afp, acnt, aever;
+};
+// The producer, staging and issuing loops of the tensor-memory M_i^-1 apply, kept out of line:
+// the kernel's long-lived per-cell values are saved once around the call instead of being
+// spilled and reloaded (from L2: the 216 KB of shared memory leave L1 almost nothing) inside
+// these loops.
+template <int N>
+__device__ __noinline__ TcStreamState tc_stream(const TcStreamArgs a, TcStreamState st) {
+  constexpr int NB = tc_nb(N), NM = 2 * NB;
+  constexpr uint32_t IDESC = tc_idesc_tf32(NM);
+  const int warp = a.warp, lane = a.lane, Ni = a.Ni, LD = a.LD, srows = a.srows, stage_floats = a.stage_floats;
+  const int nstage = a.nstage, nblk = a.nblk, SL = a.SL, spr = a.spr, nsl = a.nsl, ntl = a.ntl, nbuf = a.nbuf;
+  float* const ring = a.ring;
+  const float* const minv = a.minv;
+  const uint32_t tmem = a.tmem, bsh = a.bsh, sbo = a.sbo;
+  uint64_t* const sfull = a.sfull;
+  uint64_t* const sempty = a.sempty;
+  uint64_t* const safull = a.safull;
+  uint64_t* const saempty = a.saempty;
+  uint64_t* const sdfull = a.sdfull;
+  int* const abortp = a.abortp;
+  int* const flags = a.flags;
+  uint32_t fpar = st.fpar, epar = st.epar, ipar = st.ipar, issued = st.issued, afp = st.afp, acnt = st.acnt,
+           aever = st.aever;
+  auto acol = [&](int T, int b) { return (uint32_t)(ntl * kTcDCols + (T * nbuf + b) * 32); };
+  (void)LD;
+    if (warp == kF32Warps - 1) {
+      if (lane == 0) {
+        for (int b = 0; b < nblk && !*(volatile int*)abortp; ++b) {
+          const int s = b % nstage;
+          if (b >= nstage) {
+            if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+              atomicOr(&flags[F_TIMEOUT], 1);
+              *abortp = 1;
+              break;
+            }
+            epar ^= 1u << s;
+          }
+          const int rb = min(srows, Ni - b * srows);
+          mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
+          bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
+                   &sfull[s]);
+          issued |= 1u << s;
+          ipar ^= 1u << s;
+        }
+        for (int b = max(0, nblk - nstage); b < nblk && !*(volatile int*)abortp; ++b) {
+          const int s = b % nstage;
+          if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+            atomicOr(&flags[F_TIMEOUT], 1);
+            *abortp = 1;
+            break;
+          }
+          epar ^= 1u << s;
+        }
+      }
+    } else if (warp < kTcStagers) {
+      // staging warps: group g = warp / 4 owns tiles g, g + 3; warp quarter qq = warp % 4
+      const int g = warp >> 2, qq = warp & 3;
+      for (int s = 0; s < nsl; ++s) {
+        if (*(volatile int*)abortp) break;
+        const int b = s / spr, sl = s - b * spr, slot = b % nstage;
+        const int rb = min(srows, Ni - b * srows);
+        bool ok = true;
+        if (sl == 0) {  // the stage has arrived
+          if (lane == 0) ok = mbar_wait_bounded(&sfull[slot], (fpar >> slot) & 1u);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            if (lane == 0) {
+              atomicOr(&flags[F_TIMEOUT], 1);
+              *abortp = 1;
+            }
+            break;
+          }
+          __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
+          fpar ^= 1u << slot;
+        }
+        const float* stage = ring + (size_t)slot * stage_floats;
+        const int buf = s % nbuf;
+        for (int T = g; T < ntl; T += kTcGroups) {
+          const int bi = T * kTcBufs + buf;
+          if ((aever >> bi) & 1u) {  // the MMAs that last read this A buffer have completed
+            if (lane == 0) ok = mbar_wait_bounded(&saempty[bi], ((acnt >> bi) & 1u) ^ 1u);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
+            tc_fence_after();
+          }
+          const int mrow = T * 128 + qq * 32 + lane;
+          const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + acol(T, buf);
+          // the slice's columns k of this thread's row of M_i^-1: every shared-memory load
+          // first, then the tensor-memory stores (a load issued behind a store waits for it)
+          const int kend = (mrow < Ni) ? min(SL, rb - sl * SL) : 0;
+          const float* src = stage + (size_t)(sl * SL) * LD + mrow;
+          float x[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) x[i] = (i < kend) ? src[i * LD] : 0.f;
+          tmem_st8v(ta, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7]);
+          tmem_st8v(ta + 16, x[0] - tf32_trunc(x[0]), x[1] - tf32_trunc(x[1]), x[2] - tf32_trunc(x[2]),
+                    x[3] - tf32_trunc(x[3]), x[4] - tf32_trunc(x[4]), x[5] - tf32_trunc(x[5]),
+                    x[6] - tf32_trunc(x[6]), x[7] - tf32_trunc(x[7]));
+          if (SL == 16) {
+            tmem_st8v(ta + 8, x[8], x[9], x[10], x[11], x[12], x[13], x[14], x[15]);
+            tmem_st8v(ta + 24, x[8] - tf32_trunc(x[8]), x[9] - tf32_trunc(x[9]), x[10] - tf32_trunc(x[10]),
+                      x[11] - tf32_trunc(x[11]), x[12] - tf32_trunc(x[12]), x[13] - tf32_trunc(x[13]),
+                      x[14] - tf32_trunc(x[14]), x[15] - tf32_trunc(x[15]));
+          }
+          acnt ^= 1u << bi;  // the issuer commits once per tile and slice
+          aever |= 1u << bi;
+        }
+        if (!ok) {
+          if (lane == 0) {
+            atomicOr(&flags[F_TIMEOUT], 1);
+            *abortp = 1;
+          }
+          break;
+        }
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          for (int T = g; T < ntl; T += kTcGroups) mbar_arrive(&safull[T * kTcBufs + buf]);
+          if (sl == spr - 1 || s == nsl - 1) mbar_arrive(&sempty[slot]);  // stage read
+        }
+      }
+    } else if (warp < kTcStagers + kTcGroups && lane == 0) {
+      // issuing thread of group g: per slice and tile, once the four staging warps have
+      // filled the A buffer, D_T += A_hi [B_hi | B_lo] + A_lo [B_hi | B_lo] per 8 columns
+      const int g = warp - kTcStagers;
+      for (int s = 0; s < nsl; ++s) {
+        if (*(volatile int*)abortp) break;
+        const int buf = s % nbuf;
+        bool ok = true;
+        for (int T = g; T < ntl; T += kTcGroups) {
+          const int bi = T * kTcBufs + buf;
+          if (!mbar_wait_bounded(&safull[bi], (afp >> bi) & 1u)) {
+            ok = false;
+            break;
+          }
+          afp ^= 1u << bi;
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(T * kTcDCols);
+          const uint32_t a = tmem + acol(T, buf);
+          for (int j = 0; j < SL / 8; ++j) {
+            const int k0 = s * SL + 8 * j;
+            const uint64_t bd = tc_sdesc(bsh + (uint32_t)k0 * 32u, 128u, sbo);
+            tc_mma_tmem_a(d, a + 8 * j, bd, IDESC, (s | j) != 0 ? 1u : 0u);
+            tc_mma_tmem_a(d, a + 16 + 8 * j, bd, IDESC, 1u);
+          }
+          tc_commit(&saempty[bi]);
+        }
+        if (!ok) {
+          atomicOr(&flags[F_TIMEOUT], 1);
+          *abortp = 1;
+          break;
+        }
+      }
+      if (!*(volatile int*)abortp)
+        for (int T = g; T < ntl; T += kTcGroups) tc_commit(&sdfull[T]);
+    }
+  return TcStreamState{fpar, epar, ipar, issued, afp, acnt, aever};
+}
+
 // TC = true: the M_i^-1 apply on the 5th-generation tensor cores with tensor memory (tcgen05);
 // TC = false: the same product with mma.sync on the per-warp tensor-core path.
 template <int N, bool TC>
@@ -769,138 +943,41 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         const uint32_t bsh = smem_u32(bop);
         // tensor-memory columns: accumulators T * 48, then the A buffers (32 columns each)
         auto acol = [&](int T, int b) { return (uint32_t)(ntl * kTcDCols + (T * nbuf + b) * 32); };
-        if (warp == kF32Warps - 1) {
-          if (lane == 0) {
-            for (int b = 0; b < nblk && !sAbort; ++b) {
-              const int s = b % nstage;
-              if (b >= nstage) {
-                if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
-                  atomicOr(&m.flags[F_TIMEOUT], 1);
-                  sAbort = 1;
-                  break;
-                }
-                epar ^= 1u << s;
-              }
-              const int rb = min(srows, Ni - b * srows);
-              mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
-              bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
-                       &sfull[s]);
-              issued |= 1u << s;
-              ipar ^= 1u << s;
-            }
-            for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
-              const int s = b % nstage;
-              if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
-                atomicOr(&m.flags[F_TIMEOUT], 1);
-                sAbort = 1;
-                break;
-              }
-              epar ^= 1u << s;
-            }
-          }
-        } else if (warp < kTcStagers) {
-          // staging warps: group g = warp / 4 owns tiles g, g + 3; warp quarter qq = warp % 4
-          const int g = warp >> 2, qq = warp & 3;
-          for (int s = 0; s < nsl; ++s) {
-            if (*(volatile int*)&sAbort) break;
-            const int b = s / spr, sl = s - b * spr, slot = b % nstage;
-            const int rb = min(srows, Ni - b * srows);
-            bool ok = true;
-            if (sl == 0) {  // the stage has arrived
-              if (lane == 0) ok = mbar_wait_bounded(&sfull[slot], (fpar >> slot) & 1u);
-              ok = __shfl_sync(0xffffffffu, ok, 0);
-              if (!ok) {
-                if (lane == 0) {
-                  atomicOr(&m.flags[F_TIMEOUT], 1);
-                  sAbort = 1;
-                }
-                break;
-              }
-              __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
-              fpar ^= 1u << slot;
-            }
-            const float* stage = ring + (size_t)slot * stage_floats;
-            const int buf = s % nbuf;
-            for (int T = g; T < ntl; T += kTcGroups) {
-              const int bi = T * kTcBufs + buf;
-              if ((aever >> bi) & 1u) {  // the MMAs that last read this A buffer have completed
-                if (lane == 0) ok = mbar_wait_bounded(&saempty[bi], ((acnt >> bi) & 1u) ^ 1u);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
-                __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
-                tc_fence_after();
-              }
-              const int mrow = T * 128 + qq * 32 + lane;
-              const uint32_t ta = tmem + ((uint32_t)(qq * 32) << 16) + acol(T, buf);
-              // the slice's columns k of this thread's row of M_i^-1: every shared-memory load
-              // first, then the tensor-memory stores (a load issued behind a store waits for it)
-              const int kend = (mrow < Ni) ? min(SL, rb - sl * SL) : 0;
-              const float* src = stage + (size_t)(sl * SL) * LD + mrow;
-              float x[16];
-#pragma unroll
-              for (int i = 0; i < 16; ++i) x[i] = (i < kend) ? src[i * LD] : 0.f;
-              tmem_st8v(ta, x[0], x[1], x[2], x[3], x[4], x[5], x[6], x[7]);
-              tmem_st8v(ta + 16, x[0] - tf32_trunc(x[0]), x[1] - tf32_trunc(x[1]), x[2] - tf32_trunc(x[2]),
-                        x[3] - tf32_trunc(x[3]), x[4] - tf32_trunc(x[4]), x[5] - tf32_trunc(x[5]),
-                        x[6] - tf32_trunc(x[6]), x[7] - tf32_trunc(x[7]));
-              if (SL == 16) {
-                tmem_st8v(ta + 8, x[8], x[9], x[10], x[11], x[12], x[13], x[14], x[15]);
-                tmem_st8v(ta + 24, x[8] - tf32_trunc(x[8]), x[9] - tf32_trunc(x[9]), x[10] - tf32_trunc(x[10]),
-                          x[11] - tf32_trunc(x[11]), x[12] - tf32_trunc(x[12]), x[13] - tf32_trunc(x[13]),
-                          x[14] - tf32_trunc(x[14]), x[15] - tf32_trunc(x[15]));
-              }
-              acnt ^= 1u << bi;  // the issuer commits once per tile and slice
-              aever |= 1u << bi;
-            }
-            if (!ok) {
-              if (lane == 0) {
-                atomicOr(&m.flags[F_TIMEOUT], 1);
-                sAbort = 1;
-              }
-              break;
-            }
-            tmem_st_wait();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-              for (int T = g; T < ntl; T += kTcGroups) mbar_arrive(&safull[T * kTcBufs + buf]);
-              if (sl == spr - 1 || s == nsl - 1) mbar_arrive(&sempty[slot]);  // stage read
-            }
-          }
-        } else if (warp < kTcStagers + kTcGroups && lane == 0) {
-          // issuing thread of group g: per slice and tile, once the four staging warps have
-          // filled the A buffer, D_T += A_hi [B_hi | B_lo] + A_lo [B_hi | B_lo] per 8 columns
-          const int g = warp - kTcStagers;
-          for (int s = 0; s < nsl; ++s) {
-            if (*(volatile int*)&sAbort) break;
-            const int buf = s % nbuf;
-            bool ok = true;
-            for (int T = g; T < ntl; T += kTcGroups) {
-              const int bi = T * kTcBufs + buf;
-              if (!mbar_wait_bounded(&safull[bi], (afp >> bi) & 1u)) {
-                ok = false;
-                break;
-              }
-              afp ^= 1u << bi;
-              tc_fence_after();
-              const uint32_t d = tmem + (uint32_t)(T * kTcDCols);
-              const uint32_t a = tmem + acol(T, buf);
-              for (int j = 0; j < SL / 8; ++j) {
-                const int k0 = s * SL + 8 * j;
-                const uint64_t bd = tc_sdesc(bsh + (uint32_t)k0 * 32u, 128u, sbo);
-                tc_mma_tmem_a(d, a + 8 * j, bd, IDESC, (s | j) != 0 ? 1u : 0u);
-                tc_mma_tmem_a(d, a + 16 + 8 * j, bd, IDESC, 1u);
-              }
-              tc_commit(&saempty[bi]);
-            }
-            if (!ok) {
-              atomicOr(&m.flags[F_TIMEOUT], 1);
-              sAbort = 1;
-              break;
-            }
-          }
-          if (!*(volatile int*)&sAbort)
-            for (int T = g; T < ntl; T += kTcGroups) tc_commit(&sdfull[T]);
+        {
+          TcStreamArgs ta;
+          ta.warp = warp;
+          ta.lane = lane;
+          ta.Ni = Ni;
+          ta.LD = LD;
+          ta.srows = srows;
+          ta.stage_floats = stage_floats;
+          ta.nstage = nstage;
+          ta.nblk = nblk;
+          ta.SL = SL;
+          ta.spr = spr;
+          ta.nsl = nsl;
+          ta.ntl = ntl;
+          ta.nbuf = nbuf;
+          ta.ring = ring;
+          ta.minv = minv;
+          ta.tmem = tmem;
+          ta.bsh = bsh;
+          ta.sbo = sbo;
+          ta.sfull = sfull;
+          ta.sempty = sempty;
+          ta.safull = safull;
+          ta.saempty = saempty;
+          ta.sdfull = sdfull;
+          ta.abortp = &sAbort;
+          ta.flags = m.flags;
+          const TcStreamState ts = tc_stream<N>(ta, TcStreamState{fpar, epar, ipar, issued, afp, acnt, aever});
+          fpar = ts.fpar;
+          epar = ts.epar;
+          ipar = ts.ipar;
+          issued = ts.issued;
+          afp = ts.afp;
+          acnt = ts.acnt;
+          aever = ts.aever;
         }
         __syncthreads();
         if (sAbort) {
