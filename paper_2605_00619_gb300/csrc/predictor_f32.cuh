@@ -896,10 +896,16 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           }
         }
         // rows without data (time slices past N+1, padding to NB) and columns past N_i: zero
-        for (int e = tid; e < 2 * NB * Kp; e += kF32Threads) {
-          const int n = e / Kp, k = e - (e / Kp) * Kp, nh = n % NB;
-          if (k >= Ni || nh >= 5 * NTP || nh % NTP >= NT) bop[bidx(n, k)] = 0.f;
+        constexpr int NPAD = NB - 5 * NT;  // such rows per half
+        constexpr int TP = NTP - NT > 0 ? NTP - NT : 1;  // padded time slices per variable (divisor)
+        for (int e = tid; e < 2 * NPAD * Ni; e += kF32Threads) {
+          const int k = e % Ni, pr = e / Ni, half = pr / NPAD;
+          int nh = pr % NPAD;  // the nh-th row of a half that holds no data
+          nh = nh < 5 * (NTP - NT) ? (nh / TP) * NTP + NT + nh % TP : 5 * NTP + (nh - 5 * (NTP - NT));
+          bop[bidx(half * NB + nh, k)] = 0.f;
         }
+        for (int e = tid; e < 2 * NB * (Kp - Ni); e += kF32Threads)
+          bop[bidx(e / (Kp - Ni), Ni + e % (Kp - Ni))] = 0.f;
       }
       // the ring reuses the phase-1 buffers: order this thread's generic-proxy accesses to
       // them before the bulk copies (async proxy) that overwrite them; the tensor cores read
