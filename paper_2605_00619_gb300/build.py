@@ -1,7 +1,9 @@
 """Builds the C-ABI library ``lib/libafe.so`` in-tree for sm_103a (GB300).
 
-nvcc compiles the CUDA translation unit, g++ the host topology and reference-element
-code; the units are compiled in parallel and linked with ``nvcc -shared``.
+First g++ builds and runs ``gen_sref`` (csrc/gen_sref.cpp with the reference-element code),
+which writes ``lib/gen/sref_gen.cuh``: the FP32 predictor's reference-stiffness contractions
+with the matrix entries as immediates.  Then nvcc compiles the CUDA translation unit and g++
+the host topology and reference-element code, in parallel, and ``nvcc -shared`` links them.
 """
 from __future__ import annotations
 
@@ -39,7 +41,13 @@ def build(verbose: bool = False, extra_flags=None) -> str:
     objdir = os.path.join(LIBDIR, "obj")
     os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", "-I" + INCLUDE, "-I" + CSRC]
+    gendir = os.path.join(LIBDIR, "gen")
+    os.makedirs(gendir, exist_ok=True)
+    gen_exe = os.path.join(objdir, "gen_sref")
+    _run([os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-I" + CSRC, os.path.join(CSRC, "gen_sref.cpp"),
+          os.path.join(CSRC, "refelem.cpp"), "-o", gen_exe])
+    _run([gen_exe, os.path.join(gendir, "sref_gen.cuh")])
+    common = ["-O3", "-std=c++17", "-I" + INCLUDE, "-I" + CSRC, "-I" + gendir]
     extra = list(extra_flags or [])
     jobs = []
     for src in ("refelem.cpp", "topology.cpp"):

@@ -7,18 +7,19 @@
 //   srhs [N_i][24]      right-hand side sum_k A_k^T R_k, then Y, [5][NTP] per row (time
 //                       slices padded to a vector width NTP, columns padded to 24)
 // followed by one region used by the two phases in turn:
-//   phase 1: sR [CH][Nt][Np][5]  per-chunk sub-tet results R_{k,t} (gather buffer)
-//            sB [CH][3 Np][5][NTP]  pre-contracted fluxes of the chunk (time innermost)
+//   phase 1: sR  [CH][Nt][Np][5]     per-chunk sub-tet results R_{k,t} (gather buffer)
+//            sBt [CH Nt 5][KKS]      pre-contracted fluxes of the chunk, one column (k, t, v)
+//                                    of the 3 Np values (d, j) per row
 //   phase 2: ring [NSTAGE][rows][LD]  pipelined stages of M_i^-1 (as many as fit)
 // Per iteration:
 //   1. for chunks of CH sub-tets (twice as many when the cell leaves room): every thread
 //      takes (sub-tet k, node j, time t) items, evaluates the flux and pre-contracts it with
-//      dt adj(J_k) (f*, g*, h*) into B; then every thread takes a (k, v, time group, 4 rows m)
-//      tile of the reference-stiffness contraction R[t][m][v] = w_t sum_d sum_j S^_d[m][j]
-//      B_d[j][v][t] (one float4 of S^ and one float4 (wide chunks) or float2 of B per 16 or 8
-//      FMAs); after the chunk each thread adds, in registers for the
-//      nodes it owns, the chunk's incidences in (k, j) order (fixed order: the sum is
-//      bitwise reproducible and has no atomics);
+//      dt adj(J_k) (f*, g*, h*) into B^T; then every thread takes one column (k, t, v) and
+//      forms R[t][m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v][t] for all Np rows m in registers,
+//      with the universal S^ entries as instruction immediates (gen_sref.cpp writes the
+//      multiply-adds out at build time, zero entries skipped); after the chunk each thread
+//      adds, in registers for the nodes it owns, the chunk's incidences in (k, j) order (fixed
+//      order: the sum is bitwise reproducible and has no atomics);
 //   2. Y = M_i^-1 RHS with M_i^-1 streamed through shared memory in stages of `rows` rows by
 //      cp.async.bulk (TMA bulk copies, completion on an mbarrier), on the tensor cores:
 //      mma.sync m16n8k8 TF32 with each FP32 operand split into a TF32 head and tail (bit
@@ -27,15 +28,17 @@
 //      owns the 16-row tiles w, w+15, w+30 of Y (M_i^-1 is symmetric: row l of the stage
 //      serves column l);
 //      q^{r+1}[n,s] = u^[n] - sum_t K1t^-1[s,t] Y[n,t] and the residual, in registers.
-// Epilogue: vol = sum_k A_k^T sum_d S^_d^T adj(J_k) F_bar_k, and q_bar, F_bar . n on the face
-// slots, as the FP64 kernel.  Every mbarrier wait is bounded; a wait that runs out sets
-// flags[F_TIMEOUT], drains the copies in flight (bounded again) and the block returns.
+// Epilogue: vol = sum_k A_k^T sum_d S^_d^T adj(J_k) F_bar_k (the same column-per-thread
+// contraction with S^ transposed), and q_bar, F_bar . n on the face slots, as the FP64 kernel.
+// Every mbarrier wait is bounded; a wait that runs out sets flags[F_TIMEOUT], drains the
+// copies in flight (bounded again) and the block returns.
 #pragma once
 
 #include <algorithm>
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "sref_gen.cuh"  // generated at build time by gen_sref.cpp
 
 namespace afe {
 
@@ -267,8 +270,15 @@ __host__ __device__ constexpr size_t f32_up128(size_t x) { return (x + 127) / 12
 __host__ __device__ constexpr size_t f32_sR_bytes(int N, int ch) {
   return f32_up128((size_t)ch * (N + 1) * np_of(N) * 5 * 4);
 }
+// Column stride (floats) of the pre-contracted fluxes B^T[(k, t, v)][(d, j)] in shared memory:
+// 3 Np values padded to a multiple of 4 floats with an odd number of 16-byte groups (16-byte
+// rows for vector loads; the eight lanes of a quarter warp that load consecutive columns hit
+// eight different bank groups).  gen_sref.cpp emits the same stride as SrefFP32<N>::KKS.
+__host__ __device__ constexpr int f32_kks(int N) {
+  return 4 * (((3 * np_of(N) + 3) / 4) % 2 == 0 ? (3 * np_of(N) + 3) / 4 + 1 : (3 * np_of(N) + 3) / 4);
+}
 __host__ __device__ constexpr size_t f32_sB_bytes(int N, int ch) {
-  return f32_up128((size_t)ch * 3 * np_of(N) * 5 * f32_ntp(N) * 4);
+  return f32_up128((size_t)ch * (N + 1) * 5 * f32_kks(N) * 4);
 }
 __host__ __device__ constexpr size_t f32_sR_bytes(int N) { return f32_sR_bytes(N, f32_chunk(N)); }
 __host__ __device__ constexpr size_t f32_sB_bytes(int N) { return f32_sB_bytes(N, f32_chunk(N)); }
@@ -590,13 +600,10 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
                                                                         int diag, int smem_bytes) {
   constexpr int NP = np_of(N), NT = N + 1, NF = nf_of(N), SR = f32_row_stride(N);
   constexpr int NTP = f32_ntp(N), SRN = f32_rhs_stride(N), CH = f32_chunk(N);
-  constexpr int NPP = (NP + 3) / 4 * 4;  // rows of sSt padded to 16 bytes
-  constexpr int MG = NPP / 4;  // 4-row groups of R
-  static_assert(NTP >= NT, "the epilogue's [CH NT][3 NP][5] staging must fit in sB");
+  constexpr int KKS = f32_kks(N);  // column stride of B^T
+  static_assert(KKS == SrefFP32<N>::KKS && SrefFP32<N>::KK == 3 * NP, "generated contraction and layout disagree");
   constexpr int REC = f32_rec_bytes(N);  // bytes per sub-tet record
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(16) float sSt[3][NP][NPP];  // sSt[d][j][m] = S^_d[m][j] (zero padded)
-  __shared__ __align__(16) float sSo[3][NP][NPP];  // sSo[d][j][m] = S^_d[j][m] (volume term, zero padded)
   __shared__ float sD[3][NP][NP];    // nodal derivative matrices (viscous fluxes)
   __shared__ float sK[NT][NT];
   __shared__ float sW[NT];
@@ -626,18 +633,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
   unsigned char* const cell_base = p;  // per cell: sq, srhs, then {sR, sB | M_i^-1 ring}
   (void)Nmax;
 
-  for (int e = tid; e < 3 * NP * NPP; e += kF32Threads) {
-    const int d = e / (NP * NPP), j = (e / NPP) % NP, mm = e % NPP;
-    sSt[d][j][mm] = mm < NP ? (float)ref->S[d][mm][j] : 0.f;
-  }
   for (int e = tid; e < 3 * NP * NP; e += kF32Threads) {
     const int d = e / (NP * NP), r = (e / NP) % NP, c = e % NP;
-    sSo[d][r][c] = (float)ref->S[d][r][c];
     sD[d][r][c] = (float)ref->D[d][r][c];
-  }
-  if constexpr (NPP > NP) {  // zero padding columns of sSo
-    constexpr int PAD = NPP > NP ? NPP - NP : 1;
-    for (int e = tid; e < 3 * NP * PAD; e += kF32Threads) sSo[e / (NP * PAD)][(e / PAD) % NP][NP + e % PAD] = 0.f;
   }
   if (tid < NT * NT) sK[tid / NT][tid % NT] = (float)ref->K1tinv[tid / NT][tid % NT];
   if (tid < NT) sW[tid] = (float)ref->w[tid];
@@ -716,7 +714,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const bool wide = (TC ? tplan.wide : plan.wide) && !bt.narrow;
     const int CHc = wide ? 2 * CH : CH;
     float* sR = reinterpret_cast<float*>(shared_region);                          // phase 1, epilogue
-    float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc][3 NP][5][NTP]
+    float* sBc = reinterpret_cast<float*>(shared_region + f32_sR_bytes(N, CHc));  // [CHc NT 5][KKS]
     // phase 2: the ring of M_i^-1 stages (after the right-hand-side operand in the TC form)
     float* bop = reinterpret_cast<float*>(shared_region);
     float* ring = reinterpret_cast<float*>(shared_region + (TC ? f32_up128(tc_bop_bytes(N, Ni)) : 0));
@@ -792,63 +790,36 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           cend[r] = sincp[inode[r] + 1];
         }
       }
-      // one chunk size per instantiation: CHT sub-tets, contraction tiles of TW time slices
+      // one chunk size per instantiation: CHT sub-tets
       auto phase1 = [&](auto chunk_tag) {
         constexpr int CHT = decltype(chunk_tag)::value;
-        constexpr int TW = (CHT > CH) ? 4 : 2;  // 4 x 4 tiles for wide chunks, 4 x 2 otherwise
-        constexpr int TGN = NTP / TW;           // time groups per tile column
         for (int kc = 0; kc < S; kc += CHT) {
           const int nk = min(CHT, S - kc);
-          // (a) fluxes: items (k, j, t), t fastest (conflict-free stores into B)
+          // (a) fluxes: items (k, j, t), t fastest; the 15 values of an item go to the columns
+          // (k, t, v) of B^T at rows (d, j)
           for (int e = tid; e < nk * NP * NT; e += kF32Threads) {
             const int t = e % NT, j = (e / NT) % NP, kl = e / (NT * NP);
             float out[3][5];
             f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt, sD, out);
-            float* dst = sBc + ((size_t)(kl * 3 * NP + j) * 5) * NTP + t;
+            float* dst = sBc + (size_t)((kl * NT + t) * 5) * KKS + j;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
 #pragma unroll
-              for (int v = 0; v < 5; ++v) dst[(d * NP * 5 + v) * NTP] = out[d][v];
+              for (int v = 0; v < 5; ++v) dst[v * KKS + d * NP] = out[d][v];
           }
           __syncthreads();
-          // (b) R[k][t][m][v] = w_t sum_{d,j} S^_d[m][j] B[k][d j][v][t]: tile (k, v, time group,
-          // rows 4mg..4mg+3), mg fastest; one float4 of S^ and one TW-vector of B per 4 TW FMAs
-          for (int e = tid; e < nk * 5 * TGN * MG; e += kF32Threads) {
-            const int mg = e % MG, tg = (e / MG) % TGN, v = (e / (MG * TGN)) % 5, kl = e / (MG * TGN * 5);
-            float acc[TW][4];
+          // (b) R[k][t][m][v] = w_t sum_{d,j} S^_d[m][j] B^T[(k, t, v)][d j]: one column per thread,
+          // all Np rows m in registers, S^ as instruction immediates (the zero entries skipped)
+          for (int c = tid; c < nk * NT * 5; c += kF32Threads) {
+            float acc[NP];
 #pragma unroll
-            for (int h = 0; h < TW; ++h)
+            for (int i = 0; i < NP; ++i) acc[i] = 0.f;
+            SrefFP32<N>::contract(sBc + (size_t)c * KKS, acc);
+            const int kt = c / 5, v = c - kt * 5;  // kt = kl NT + t
+            const float wt = sW[kt % NT];
+            float* dst = sR + kt * NP * 5 + v;
 #pragma unroll
-              for (int i = 0; i < 4; ++i) acc[h][i] = 0.f;
-            const float* bcol = sBc + ((size_t)kl * 3 * NP * 5 + v) * NTP + TW * tg;
-            const float* scol = &sSt[0][0][4 * mg];
-#pragma unroll 6
-            for (int kk = 0; kk < 3 * NP; ++kk) {
-              const float4 s4 = *reinterpret_cast<const float4*>(scol + kk * NPP);
-              float bv[TW];
-              if constexpr (TW == 4) {
-                const float4 b4 = *reinterpret_cast<const float4*>(bcol + kk * 5 * NTP);
-                bv[0] = b4.x; bv[1] = b4.y; bv[2] = b4.z; bv[3] = b4.w;
-              } else {
-                const float2 b2 = *reinterpret_cast<const float2*>(bcol + kk * 5 * NTP);
-                bv[0] = b2.x; bv[1] = b2.y;
-              }
-#pragma unroll
-              for (int h = 0; h < TW; ++h) {
-                acc[h][0] += s4.x * bv[h]; acc[h][1] += s4.y * bv[h];
-                acc[h][2] += s4.z * bv[h]; acc[h][3] += s4.w * bv[h];
-              }
-            }
-#pragma unroll
-            for (int h = 0; h < TW; ++h) {
-              const int t = TW * tg + h;
-              if (t >= NT) continue;
-              const float wt = sW[t];
-              float* dst = sR + ((kl * NT + t) * NP + 4 * mg) * 5 + v;
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                if (4 * mg + i < NP) dst[5 * i] = wt * acc[h][i];
-            }
+            for (int i = 0; i < NP; ++i) dst[5 * i] = wt * acc[i];
           }
           __syncthreads();
           // gather this chunk's incidences, in (k, j) order, into the items' registers
@@ -1246,7 +1217,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       }
     }
     const int CHV = CHc * NT;  // sub-tets per volume chunk (sR holds CHc*NT slices)
-    float* sBv = sBc;          // [CHV][3 NP][5] time-integrated pre-contracted fluxes (fits in sB)
+    float* sBv = sBc;          // [CHV 5][KKS] time-integrated pre-contracted fluxes (fits in sB)
     for (int kc = 0; kc < S; kc += CHV) {
       const int nk = min(CHV, S - kc);
       // (a) items (k, j): B_bar[k][d j][v] = sum_t w_t dt adj(J_k) F(q_t) at node j
@@ -1266,41 +1237,24 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
 #pragma unroll
             for (int v = 0; v < 5; ++v) accb[d][v] += out[d][v];
         }
-        float* dst = sBv + ((size_t)kl * 3 * NP + j) * 5;
+        float* dst = sBv + (size_t)(kl * 5) * KKS + j;  // columns (k, v), rows (d, j)
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int v = 0; v < 5; ++v) dst[d * NP * 5 + v] = accb[d][v];
+          for (int v = 0; v < 5; ++v) dst[v * KKS + d * NP] = accb[d][v];
       }
       __syncthreads();
-      // (b) R_bar[k][m][v] = sum_{d,j} S^_d[j][m] B_bar[k][d j][v]: tile (k, rows 4mg..4mg+3, all v)
-      for (int e = tid; e < nk * MG; e += kF32Threads) {
-        const int kl = e / MG, mg = e % MG;
-        float acc[4][5];
+      // (b) R_bar[k][m][v] = sum_{d,j} S^_d[j][m] B_bar^T[(k, v)][d j]: one column per thread, all
+      // Np rows in registers, S^ as instruction immediates
+      for (int c = tid; c < nk * 5; c += kF32Threads) {
+        float acc[NP];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < NP; ++i) acc[i] = 0.f;
+        SrefFP32<N>::contract_t(sBv + (size_t)c * KKS, acc);
+        const int kl = c / 5, v = c - kl * 5;
+        float* dst = sR + kl * NP * 5 + v;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) acc[i][v] = 0.f;
-        const float* bk = sBv + (size_t)kl * 3 * NP * 5;
-        const float* scol = &sSo[0][0][4 * mg];
-#pragma unroll 4
-        for (int kk = 0; kk < 3 * NP; ++kk) {
-          const float4 s4 = *reinterpret_cast<const float4*>(scol + kk * NPP);
-          const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const float b = bk[kk * 5 + v];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i][v] += sv[i] * b;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (4 * mg + i < NP) {
-            float* dst = sR + (kl * NP + 4 * mg + i) * 5;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) dst[v] = acc[i][v];
-          }
+        for (int i = 0; i < NP; ++i) dst[5 * i] = acc[i];
       }
       __syncthreads();
 #pragma unroll
