@@ -10,7 +10,9 @@
 //   phase 1: sR  [CH][Nt][Np][5]     per-chunk sub-tet results R_{k,t} (gather buffer)
 //            sBt [CH Nt 5][KKS]      pre-contracted fluxes of the chunk, one column (k, t, v)
 //                                    of the 3 Np values (d, j) per row
-//   phase 2: ring [NSTAGE][rows][LD]  pipelined stages of M_i^-1 (as many as fit)
+//   phase 2: ring [NSTAGE][rows][LD]  pipelined stages of M_i^-1 (as many as fit), at the top
+//                                     of the region: its first slot above the phase-1 buffers
+//                                     when there is room, filled while phase 1 runs
 // Per iteration:
 //   1. for chunks of CH sub-tets (twice as many when the cell leaves room): every thread
 //      takes (sub-tet k, node j, time t) items, evaluates the flux and pre-contracts it with
@@ -376,13 +378,12 @@ inline size_t predictor_f32_smem(int N, int Nmax, int Smax) {
          std::max(phase1, stage);
 }
 
-// flux pre-contraction at one (sub-tet, time, local node j): out[d][v] = sum_e G[d][e] F_e[v]
-// with G = scale * adj(J); gradients (viscous only) from the sub-tet's own polynomial
+// physical flux F_e[v] at one (sub-tet, time, local node j); gradients (viscous only) from the
+// sub-tet's own polynomial
 template <int N>
-__device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, const uint16_t* __restrict__ Ak,
-                                                  const float* __restrict__ g, int j, int t, bool visc, float mu,
-                                                  float kap, float gam, float Rg, float scale,
-                                                  const float (*sD)[np_of(N)][np_of(N)], float out[3][5]) {
+__device__ __forceinline__ void f32_flux(const float* __restrict__ sq, const uint16_t* __restrict__ Ak,
+                                         const float* __restrict__ g, int j, int t, bool visc, float mu, float kap,
+                                         float gam, float Rg, const float (*sD)[np_of(N)][np_of(N)], float F[3][5]) {
   constexpr int NP = np_of(N), SQ = f32_row_stride(N);
   float Q[5];
   const float* qn = sq + Ak[j] * SQ + t * 5;
@@ -410,12 +411,24 @@ __device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, 
 #pragma unroll
       for (int v = 0; v < 5; ++v) gq[e][v] = (g[0 * 3 + e] * gx[0][v] + g[1 * 3 + e] * gx[1][v] + g[2 * 3 + e] * gx[2][v]) * idet;
   }
-  float F[3][5];
   phys_flux<float>(Q, gq, visc, mu, kap, gam, Rg, F);
+}
+// flux pre-contraction: out[d][v] = scale sum_e adj(J)[d][e] F_e[v]
+__device__ __forceinline__ void f32_contract_adj(const float* __restrict__ g, float scale, const float (&F)[3][5],
+                                                 float out[3][5]) {
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int v = 0; v < 5; ++v) out[d][v] = scale * (g[d * 3 + 0] * F[0][v] + g[d * 3 + 1] * F[1][v] + g[d * 3 + 2] * F[2][v]);
+}
+template <int N>
+__device__ __forceinline__ void f32_flux_contract(const float* __restrict__ sq, const uint16_t* __restrict__ Ak,
+                                                  const float* __restrict__ g, int j, int t, bool visc, float mu,
+                                                  float kap, float gam, float Rg, float scale,
+                                                  const float (*sD)[np_of(N)][np_of(N)], float out[3][5]) {
+  float F[3][5];
+  f32_flux<N>(sq, Ak, g, j, t, visc, mu, kap, gam, Rg, sD, F);
+  f32_contract_adj(g, scale, F, out);
 }
 
 // Inputs of the tensor-memory apply's streaming loops (one cell-iteration).
@@ -722,6 +735,18 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     const int stage_floats = srows * LD;
     const int nstage = min(TC ? tplan.nstage : plan.nstage, bt.ring_cap > 0 ? bt.ring_cap : kF32MaxStages);
     const int nblk = (Ni + srows - 1) / srows;
+    // mma.sync form: the ring sits at the top of the shared region, slot s at top - (s + 1)
+    // stages, so that slot 0 lies above the phase-1 buffers whenever the region leaves room
+    // for a stage there; then the first stage of M_i^-1 is loaded while phase 1 runs (npre).
+    const size_t region_top =
+        ((size_t)smem_bytes - (size_t)(shared_region - smem_raw)) / 128 * 128;  // bytes of the region
+    float* const ring_top = reinterpret_cast<float*>(shared_region + region_top);
+    auto slot_ptr = [&](int sl) -> float* {
+      return TC ? ring + (size_t)sl * stage_floats : ring_top - (size_t)(sl + 1) * stage_floats;
+    };
+    const int npre = (!TC && nblk > 0 && nstage > 0 &&
+                      region_top >= f32_sR_bytes(N, CHc) + f32_sB_bytes(N, CHc) + (size_t)stage_floats * 4)
+                         ? 1 : 0;
 
     // the cell's sub-tet records arrive by one bulk copy while the state is loaded
     if (tid == 0) {
@@ -763,6 +788,9 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     // thread 0 observed the copy's completion (acquire); the barrier above orders the records
     // for every thread (a wait by all 512 threads would be 512 serialised barrier tests)
     phase ^= 1u;
+    // the first stage's bulk copy may overwrite memory that earlier generic accesses (the
+    // last cell's buffers) used: order them first (every thread, then the barrier)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
 
     constexpr int NNT = (5 * NTP + 7) / 8;  // 8-column tiles of Y
@@ -774,6 +802,15 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
     bool conv = false;
     while (!conv && it < m.picard_max) {
       ++it;
+      // the first stage of M_i^-1 for this iteration's apply, into slot 0 above the phase-1
+      // buffers (the ring was drained at the end of the last apply)
+      if (npre && warp == kF32Warps - 1 && lane == 0) {
+        const int rb = min(kF32Rows, Ni);
+        mbar_expect_tx(&sfull[0], (uint32_t)(rb * LD * 4));
+        bulk_g2s(slot_ptr(0), minv, (uint32_t)(rb * LD * 4), &sfull[0]);
+        issued |= 1u;
+        ipar ^= 1u;
+      }
       // ---- 1. right-hand side RHS[n][t] = sum over incidences (k, j) of R_{k,t}[j]
       // gather items of this thread: (node, time slice) = (i / NT, i % NT), i = tid + 512 r
       int inode[kF32Items], cur[kF32Items], cend[kF32Items];
@@ -1026,7 +1063,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             for (int i = 0; i < 4; ++i) cacc[r][nt][i] = 0.f;
         if (!consumer) {
           if (lane == 0) {
-            for (int b = 0; b < nblk && !sAbort; ++b) {
+            for (int b = npre; b < nblk && !sAbort; ++b) {
               const int s = b % nstage;
               if (b >= nstage) {
                 if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
@@ -1038,8 +1075,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
               }
               const int rb = min(srows, Ni - b * srows);
               mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
-              bulk_g2s(ring + (size_t)s * stage_floats, minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4),
-                       &sfull[s]);
+              bulk_g2s(slot_ptr(s), minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4), &sfull[s]);
               issued |= 1u << s;
               ipar ^= 1u << s;
             }
@@ -1071,7 +1107,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             }
             __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
             fpar ^= 1u << s;
-            const float* stage = ring + (size_t)s * stage_floats;
+            const float* stage = slot_ptr(s);
             const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
             // one 8-row k-step: B fragments (RHS rows) for every column tile, then per row tile the
             // A fragments (M_i^-1 rows) and three rounds of MMAs over the column tiles
@@ -1223,20 +1259,23 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       // (a) items (k, j): B_bar[k][d j][v] = sum_t w_t dt adj(J_k) F(q_t) at node j
       for (int e = tid; e < nk * NP; e += kF32Threads) {
         const int kl = e / NP, j = e % NP;
-        float accb[3][5];
+        // F_bar = sum_t w_t F(q_t), then dt adj(J) F_bar once
+        float fbar[3][5];
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int v = 0; v < 5; ++v) accb[d][v] = 0.f;
+          for (int v = 0; v < 5; ++v) fbar[d][v] = 0.f;
         for (int t = 0; t < NT; ++t) {
-          float out[3][5];
-          f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt * sW[t], sD,
-                               out);
+          float F[3][5];
+          f32_flux<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, sD, F);
+          const float wt = sW[t];
 #pragma unroll
           for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) accb[d][v] += out[d][v];
+            for (int v = 0; v < 5; ++v) fbar[d][v] += wt * F[d][v];
         }
+        float accb[3][5];
+        f32_contract_adj(rec_g(kc + kl), dt, fbar, accb);
         float* dst = sBv + (size_t)(kl * 5) * KKS + j;  // columns (k, v), rows (d, j)
 #pragma unroll
         for (int d = 0; d < 3; ++d)
