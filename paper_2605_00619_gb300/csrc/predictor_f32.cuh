@@ -871,19 +871,82 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           // which overwrites sR, starts after the barrier that follows those items
         }
       };
-      if constexpr (NTP == 4) {
+      // First iteration of the mma.sync form: q^0 = u^ at every time node (the initial guess),
+      // so the fluxes at the N+1 time nodes are equal and R_{k,t} = w_t R_k with R_k the
+      // contraction of the time-independent flux; the right-hand side is RHS[n][t] =
+      // w_t sum_{(k, j) at n} R_k[j].  One flux per (sub-tet, node) and one column per
+      // (sub-tet, variable) then serve all time slices, in chunks of CHc (N+1) sub-tets (the
+      // buffers of the volume term's layout).
+      const bool first_const = !TC && it == 1;
+      if (first_const) {
+        float facc[2][5];
+        int fcur[2], fend[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int n = tid + r * kF32Threads;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) facc[r][v] = 0.f;
+          fcur[r] = n < Ni ? sincp[n] : 0;
+          fend[r] = n < Ni ? sincp[n + 1] : 0;
+        }
+        const int CH1 = CHc * NT;  // sub-tets per chunk: [CH1 5][KKS] fits in sB, [CH1][NP][5] in sR
+        for (int kc = 0; kc < S; kc += CH1) {
+          const int nk = min(CH1, S - kc);
+          for (int e = tid; e < nk * NP; e += kF32Threads) {
+            const int kl = e / NP, j = e % NP;
+            float out[3][5];
+            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, 0, visc, mu, kap, gam, Rg, dt, sD, out);
+            float* dst = sBc + (size_t)(kl * 5) * KKS + j;  // columns (k, v), rows (d, j)
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+              for (int v = 0; v < 5; ++v) dst[v * KKS + d * NP] = out[d][v];
+          }
+          __syncthreads();
+          for (int c = tid; c < nk * 5; c += kF32Threads) {
+            float acc[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) acc[i] = 0.f;
+            SrefFP32<N>::contract(sBc + (size_t)c * KKS, acc);
+            const int kl = c / 5, v = c - kl * 5;
+            float* dst = sR + kl * NP * 5 + v;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) dst[5 * i] = acc[i];
+          }
+          __syncthreads();
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+            gather_in_order(inc, fcur[r], fend[r], kc, nk, [&](int k, int j) { return sR + (k * NP + j) * 5; },
+                            facc[r]);
+          // no barrier here: the next chunk's flux items write only sB, and its contraction,
+          // which overwrites sR, starts after the barrier that follows those items
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int n = tid + r * kF32Threads;
+          if (n >= Ni) continue;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const float wt = sW[t];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) srhs[n * SRN + v * NTP + t] = wt * facc[r][v];
+          }
+        }
+      } else if constexpr (NTP == 4) {
         if (wide) phase1(std::integral_constant<int, 2 * CH>{});
         else phase1(std::integral_constant<int, CH>{});
       } else {
         phase1(std::integral_constant<int, CH>{});
       }
       if constexpr (!TC) {
+        if (!first_const) {
 #pragma unroll
-        for (int r = 0; r < kF32Items; ++r) {
-          if (inode[r] < 0) continue;
-          const int t = (tid + r * kF32Threads) % NT;
+          for (int r = 0; r < kF32Items; ++r) {
+            if (inode[r] < 0) continue;
+            const int t = (tid + r * kF32Threads) % NT;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v * NTP + t] = racc[r][v];
+            for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v * NTP + t] = racc[r][v];
+          }
         }
       } else {
         // the right-hand-side operand B = [RHS | RHS - tf32(RHS)] (2 NB rows, K = the cell's
