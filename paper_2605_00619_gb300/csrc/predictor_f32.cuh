@@ -16,12 +16,15 @@
 // Per iteration:
 //   1. for chunks of CH sub-tets (twice as many when the cell leaves room): every thread
 //      takes (sub-tet k, node j, time t) items, evaluates the flux and pre-contracts it with
-//      dt adj(J_k) (f*, g*, h*) into B^T; then every thread takes one column (k, t, v) and
-//      forms R[t][m][v] = w_t sum_d sum_j S^_d[m][j] B_d[j][v][t] for all Np rows m in registers,
+//      adj(J_k) (f*, g*, h*) into B^T; then every thread takes one column (k, t, v) and forms
+//      R[t][m][v] = w_t dt sum_d sum_j S^_d[m][j] B_d[j][v][t] for all Np rows m in registers,
 //      with the universal S^ entries as instruction immediates (gen_sref.cpp writes the
 //      multiply-adds out at build time, zero entries skipped); after the chunk each thread
 //      adds, in registers for the nodes it owns, the chunk's incidences in (k, j) order (fixed
 //      order: the sum is bitwise reproducible and has no atomics);
+//      The first iteration starts from q^0 = u^, the same at every time node: one flux per
+//      (k, j) and one column per (k, v) serve all time slices (R_{k,t} = w_t R_k) and the apply
+//      takes the 5 time-independent columns (Y_t = w_t Y_0);
 //   2. Y = M_i^-1 RHS with M_i^-1 streamed through shared memory in stages of `rows` rows by
 //      cp.async.bulk (TMA bulk copies, completion on an mbarrier), on the tensor cores:
 //      mma.sync m16n8k8 TF32 with each FP32 operand split into a TF32 head and tail (bit
@@ -837,7 +840,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           for (int e = tid; e < nk * NP * NT; e += kF32Threads) {
             const int t = e % NT, j = (e / NT) % NP, kl = e / (NT * NP);
             float out[3][5];
-            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, dt, sD, out);
+            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, 1.f, sD, out);
             float* dst = sBc + (size_t)((kl * NT + t) * 5) * KKS + j;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
@@ -853,7 +856,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
             for (int i = 0; i < NP; ++i) acc[i] = 0.f;
             SrefFP32<N>::contract(sBc + (size_t)c * KKS, acc);
             const int kt = c / 5, v = c - kt * 5;  // kt = kl NT + t
-            const float wt = sW[kt % NT];
+            const float wt = sW[kt % NT] * dt;  // the time weight and dt, applied once per column
             float* dst = sR + kt * NP * 5 + v;
 #pragma unroll
             for (int i = 0; i < NP; ++i) dst[5 * i] = wt * acc[i];
@@ -873,10 +876,11 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
       };
       // First iteration of the mma.sync form: q^0 = u^ at every time node (the initial guess),
       // so the fluxes at the N+1 time nodes are equal and R_{k,t} = w_t R_k with R_k the
-      // contraction of the time-independent flux; the right-hand side is RHS[n][t] =
-      // w_t sum_{(k, j) at n} R_k[j].  One flux per (sub-tet, node) and one column per
-      // (sub-tet, variable) then serve all time slices, in chunks of CHc (N+1) sub-tets (the
-      // buffers of the volume term's layout).
+      // contraction of the time-independent flux; the right-hand side is RHS[n][t] = w_t r[n]
+      // with r[n] = sum_{(k, j) at n} R_k[j], and Y[n][t] = w_t (M_i^-1 r)[n].  One flux per
+      // (sub-tet, node) and one column per (sub-tet, variable) serve all time slices, in
+      // chunks of CHc (N+1) sub-tets (the buffers of the volume term's layout), and the apply
+      // takes the 5 columns of r (one 8-column tile) instead of 5 (N+1).
       const bool first_const = !TC && it == 1;
       if (first_const) {
         float facc[2][5];
@@ -895,7 +899,7 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           for (int e = tid; e < nk * NP; e += kF32Threads) {
             const int kl = e / NP, j = e % NP;
             float out[3][5];
-            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, 0, visc, mu, kap, gam, Rg, dt, sD, out);
+            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, 0, visc, mu, kap, gam, Rg, 1.f, sD, out);
             float* dst = sBc + (size_t)(kl * 5) * KKS + j;  // columns (k, v), rows (d, j)
 #pragma unroll
             for (int d = 0; d < 3; ++d)
@@ -921,16 +925,13 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           // no barrier here: the next chunk's flux items write only sB, and its contraction,
           // which overwrites sR, starts after the barrier that follows those items
         }
+        // r in columns 0..4 (columns 5..7 of the tile are still zero from the cell's start)
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int n = tid + r * kF32Threads;
           if (n >= Ni) continue;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            const float wt = sW[t];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) srhs[n * SRN + v * NTP + t] = wt * facc[r][v];
-          }
+          for (int v = 0; v < 5; ++v) srhs[n * SRN + v] = dt * facc[r][v];
         }
       } else if constexpr (NTP == 4) {
         if (wide) phase1(std::integral_constant<int, 2 * CH>{});
@@ -1117,18 +1118,38 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         // for mt = w, w + 15, w + 30 with 3xTF32 mma.sync; per 8-row k-step of a stage it loads
         // the B fragments (RHS rows) once for all column tiles and the A fragments (M_i^-1
         // rows = columns) once per row tile.
-        float cacc[3][NNT][4];
+        // the consumer loops and Y's write-out for NT1 8-column tiles of RHS / Y: one in the
+        // first iteration (the 5 time-independent columns), 5 (N+1) / 8 rounded up otherwise
+        auto apply = [&](auto nt_tag) {
+          constexpr int NT1 = decltype(nt_tag)::value;
+          float cacc[3][NT1][4];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+          for (int r = 0; r < 3; ++r)
 #pragma unroll
-          for (int nt = 0; nt < NNT; ++nt)
+            for (int nt = 0; nt < NT1; ++nt)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) cacc[r][nt][i] = 0.f;
-        if (!consumer) {
-          if (lane == 0) {
-            for (int b = npre; b < nblk && !sAbort; ++b) {
-              const int s = b % nstage;
-              if (b >= nstage) {
+              for (int i = 0; i < 4; ++i) cacc[r][nt][i] = 0.f;
+          if (!consumer) {
+            if (lane == 0) {
+              for (int b = npre; b < nblk && !sAbort; ++b) {
+                const int s = b % nstage;
+                if (b >= nstage) {
+                  if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
+                    atomicOr(&m.flags[F_TIMEOUT], 1);
+                    sAbort = 1;
+                    break;
+                  }
+                  epar ^= 1u << s;
+                }
+                const int rb = min(srows, Ni - b * srows);
+                mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
+                bulk_g2s(slot_ptr(s), minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4), &sfull[s]);
+                issued |= 1u << s;
+                ipar ^= 1u << s;
+              }
+              // every stage released by the consumers before the ring is reused
+              for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
+                const int s = b % nstage;
                 if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
                   atomicOr(&m.flags[F_TIMEOUT], 1);
                   sAbort = 1;
@@ -1136,86 +1157,96 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
                 }
                 epar ^= 1u << s;
               }
-              const int rb = min(srows, Ni - b * srows);
-              mbar_expect_tx(&sfull[s], (uint32_t)(rb * LD * 4));
-              bulk_g2s(slot_ptr(s), minv + (size_t)b * stage_floats, (uint32_t)(rb * LD * 4), &sfull[s]);
-              issued |= 1u << s;
-              ipar ^= 1u << s;
             }
-            // every stage released by the consumers before the ring is reused
-            for (int b = max(0, nblk - nstage); b < nblk && !sAbort; ++b) {
+          } else {
+            for (int b = 0; b < nblk; ++b) {
               const int s = b % nstage;
-              if (!mbar_wait_bounded(&sempty[s], (epar >> s) & 1u)) {
-                atomicOr(&m.flags[F_TIMEOUT], 1);
-                sAbort = 1;
+              // lane 0 waits (bounded); the warp follows its verdict, so that no lane leaves the
+              // loop alone
+              bool ok = true;
+              if (lane == 0) ok = mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
+              ok = __shfl_sync(0xffffffffu, ok, 0);
+              if (!ok) {
+                if (lane == 0) {
+                  atomicOr(&m.flags[F_TIMEOUT], 1);
+                  sAbort = 1;
+                }
                 break;
               }
-              epar ^= 1u << s;
+              __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
+              fpar ^= 1u << s;
+              const float* stage = slot_ptr(s);
+              const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
+              // one 8-row k-step: B fragments (RHS rows) for every column tile, then per row tile the
+              // A fragments (M_i^-1 rows) and three rounds of MMAs over the column tiles
+              auto kstep = [&](int ks, bool full) {
+                const int k0 = ks * 8 + tq, k1 = k0 + 4;  // stage rows of this lane's fragments
+                const bool v0 = full || k0 < rb, v1 = full || k1 < rb;  // rows past N_i give zero
+                uint32_t bh[NT1][2], bl[NT1][2];
+#pragma unroll
+                for (int nt = 0; nt < NT1; ++nt) {
+                  const float x0 = v0 ? srhs[(l0 + k0) * SRN + nt * 8 + gq] : 0.f;
+                  const float x1 = v1 ? srhs[(l0 + k1) * SRN + nt * 8 + gq] : 0.f;
+                  tf32_split(x0, bh[nt][0], bl[nt][0]);
+                  tf32_split(x1, bh[nt][1], bl[nt][1]);
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                  const int mt = warp + r * kF32Consumers;
+                  if (mt >= nmt) break;
+                  const float* arow0 = stage + k0 * LD + mt * 16 + gq;
+                  const float* arow1 = stage + k1 * LD + mt * 16 + gq;
+                  uint32_t ah[4], al[4];
+                  tf32_split(v0 ? arow0[0] : 0.f, ah[0], al[0]);
+                  tf32_split(v0 ? arow0[8] : 0.f, ah[1], al[1]);
+                  tf32_split(v1 ? arow1[0] : 0.f, ah[2], al[2]);
+                  tf32_split(v1 ? arow1[8] : 0.f, ah[3], al[3]);
+#pragma unroll
+                  for (int nt = 0; nt < NT1; ++nt)
+                    mma_tf32(cacc[r][nt], al, bh[nt][0], bh[nt][1]);
+#pragma unroll
+                  for (int nt = 0; nt < NT1; ++nt)
+                    mma_tf32(cacc[r][nt], ah, bl[nt][0], bl[nt][1]);
+#pragma unroll
+                  for (int nt = 0; nt < NT1; ++nt)
+                    mma_tf32(cacc[r][nt], ah, bh[nt][0], bh[nt][1]);
+                }
+              };
+              if (rb == kF32Rows) {  // full stage: no row masks
+#pragma unroll
+                for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, true);
+              } else {
+#pragma unroll
+                for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, false);
+              }
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sempty[s]);
             }
           }
-        } else {
-          for (int b = 0; b < nblk; ++b) {
-            const int s = b % nstage;
-            // lane 0 waits (bounded); the warp follows its verdict, so that no lane leaves the
-            // loop alone
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait_bounded(&sfull[s], (fpar >> s) & 1u);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-              if (lane == 0) {
-                atomicOr(&m.flags[F_TIMEOUT], 1);
-                sAbort = 1;
+          __syncthreads();  // every thread has finished reading RHS and the ring is drained
+          if (sAbort) return;
+          if (consumer)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              const int mt = warp + r * kF32Consumers;
+              if (mt >= nmt) break;
+              const int n0r = mt * 16 + gq, n1r = n0r + 8;
+#pragma unroll
+              for (int nt = 0; nt < NT1; ++nt) {
+                const int col = nt * 8 + 2 * tq;
+                if (n0r < Ni) {
+                  srhs[n0r * SRN + col] = cacc[r][nt][0];
+                  srhs[n0r * SRN + col + 1] = cacc[r][nt][1];
+                }
+                if (n1r < Ni) {
+                  srhs[n1r * SRN + col] = cacc[r][nt][2];
+                  srhs[n1r * SRN + col + 1] = cacc[r][nt][3];
+                }
               }
-              break;
             }
-            __syncwarp();  // lane 0 observed the phase (acquire); the warp barrier orders the rest
-            fpar ^= 1u << s;
-            const float* stage = slot_ptr(s);
-            const int l0 = b * kF32Rows, rb = min(kF32Rows, Ni - l0);
-            // one 8-row k-step: B fragments (RHS rows) for every column tile, then per row tile the
-            // A fragments (M_i^-1 rows) and three rounds of MMAs over the column tiles
-            auto kstep = [&](int ks, bool full) {
-              const int k0 = ks * 8 + tq, k1 = k0 + 4;  // stage rows of this lane's fragments
-              const bool v0 = full || k0 < rb, v1 = full || k1 < rb;  // rows past N_i give zero
-              uint32_t bh[NNT][2], bl[NNT][2];
-#pragma unroll
-              for (int nt = 0; nt < NNT; ++nt) {
-                const float x0 = v0 ? srhs[(l0 + k0) * SRN + nt * 8 + gq] : 0.f;
-                const float x1 = v1 ? srhs[(l0 + k1) * SRN + nt * 8 + gq] : 0.f;
-                tf32_split(x0, bh[nt][0], bl[nt][0]);
-                tf32_split(x1, bh[nt][1], bl[nt][1]);
-              }
-#pragma unroll
-              for (int r = 0; r < 3; ++r) {
-                const int mt = warp + r * kF32Consumers;
-                if (mt >= nmt) break;
-                const float* arow0 = stage + k0 * LD + mt * 16 + gq;
-                const float* arow1 = stage + k1 * LD + mt * 16 + gq;
-                uint32_t ah[4], al[4];
-                tf32_split(v0 ? arow0[0] : 0.f, ah[0], al[0]);
-                tf32_split(v0 ? arow0[8] : 0.f, ah[1], al[1]);
-                tf32_split(v1 ? arow1[0] : 0.f, ah[2], al[2]);
-                tf32_split(v1 ? arow1[8] : 0.f, ah[3], al[3]);
-#pragma unroll
-                for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], al, bh[nt][0], bh[nt][1]);
-#pragma unroll
-                for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bl[nt][0], bl[nt][1]);
-#pragma unroll
-                for (int nt = 0; nt < NNT; ++nt) mma_tf32(cacc[r][nt], ah, bh[nt][0], bh[nt][1]);
-              }
-            };
-            if (rb == kF32Rows) {  // full stage: no row masks
-#pragma unroll
-              for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, true);
-            } else {
-#pragma unroll
-              for (int ks = 0; ks < kF32Rows / 8; ++ks) kstep(ks, false);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sempty[s]);
-          }
-        }
-        __syncthreads();  // every thread has finished reading RHS and the ring is drained
+        };
+        if (first_const) apply(std::integral_constant<int, 1>{});
+        else apply(std::integral_constant<int, NNT>{});
         if (sAbort) {
           // a bounded wait ran out (flags[F_TIMEOUT] is set): wait (bounded) for the last copy
           // issued into every slot (the phase its completion ends), then leave
@@ -1225,31 +1256,22 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           __syncthreads();
           goto kernel_exit;
         }
-        if (consumer)
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const int mt = warp + r * kF32Consumers;
-            if (mt >= nmt) break;
-            const int n0r = mt * 16 + gq, n1r = n0r + 8;
-#pragma unroll
-            for (int nt = 0; nt < NNT; ++nt) {
-              const int col = nt * 8 + 2 * tq;
-              if (n0r < Ni) {
-                srhs[n0r * SRN + col] = cacc[r][nt][0];
-                srhs[n0r * SRN + col + 1] = cacc[r][nt][1];
-              }
-              if (n1r < Ni) {
-                srhs[n1r * SRN + col] = cacc[r][nt][2];
-                srhs[n1r * SRN + col + 1] = cacc[r][nt][3];
-              }
-            }
-          }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
           const int n = tid + r * kF32Threads;
           if (n >= Ni) continue;
           float y[NT][5];
+          if (first_const) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              const float y0 = srhs[n * SRN + v];
+#pragma unroll
+              for (int t = 0; t < NT; ++t) y[t][v] = sW[t] * y0;
+            }
+            update_node(n, y);
+            continue;
+          }
 #pragma unroll
           for (int v = 0; v < 5; ++v) {  // one vector load per variable
             float yv[NTP];
