@@ -204,7 +204,7 @@ void launch_face(const StepPlan& P) {
 template <int N, typename Real>
 afe_status launch_corrector(const StepPlan& P) {
   if (sizeof(Real) == 4 && corrector_f32_fits(P.b->Nmax)) {
-    const size_t smem = (size_t)P.b->Nmax * 5 * sizeof(float);
+    const size_t smem = (size_t)P.b->Nmax * 10 * sizeof(float);
     if (smem > 48 * 1024)
       AFE_CUDA(cudaFuncSetAttribute(afe::corrector_f32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));

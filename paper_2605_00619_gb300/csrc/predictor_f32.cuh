@@ -815,13 +815,21 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
         ipar ^= 1u;
       }
       // ---- 1. right-hand side RHS[n][t] = sum over incidences (k, j) of R_{k,t}[j]
-      // gather items of this thread: (node, time slice) = (i / NT, i % NT), i = tid + 512 r
+      // First iteration of the mma.sync form: q^0 = u^ at every time node (the initial guess),
+      // so the fluxes at the N+1 time nodes are equal and R_{k,t} = w_t R_k with R_k the
+      // contraction of the time-independent flux; the right-hand side is RHS[n][t] = w_t r[n]
+      // with r[n] = sum_{(k, j) at n} R_k[j], and Y[n][t] = w_t (M_i^-1 r)[n].  The same code
+      // then runs with one time slice (NTe = 1, weight 1) on chunks (N+1) times as wide, and
+      // the apply takes the 5 columns of r (one 8-column tile) instead of 5 (N+1).
+      const bool first_const = !TC && it == 1;
+      const int NTe = first_const ? 1 : NT;
+      // gather items of this thread: (node, time slice) = (i / NTe, i % NTe), i = tid + 512 r
       int inode[kF32Items], cur[kF32Items], cend[kF32Items];
       float racc[kF32Items][5];
 #pragma unroll
       for (int r = 0; r < kF32Items; ++r) {
         const int i = tid + r * kF32Threads;
-        inode[r] = i < Ni * NT ? i / NT : -1;
+        inode[r] = i < Ni * NTe ? (first_const ? i : i / NT) : -1;
         cur[r] = cend[r] = 0;
 #pragma unroll
         for (int v = 0; v < 5; ++v) racc[r][v] = 0.f;
@@ -830,117 +838,59 @@ __global__ void __launch_bounds__(kF32Threads, 1) predictor_f32_kernel(const __g
           cend[r] = sincp[inode[r] + 1];
         }
       }
-      // one chunk size per instantiation: CHT sub-tets
-      auto phase1 = [&](auto chunk_tag) {
-        constexpr int CHT = decltype(chunk_tag)::value;
-        for (int kc = 0; kc < S; kc += CHT) {
-          const int nk = min(CHT, S - kc);
-          // (a) fluxes: items (k, j, t), t fastest; the 15 values of an item go to the columns
-          // (k, t, v) of B^T at rows (d, j)
-          for (int e = tid; e < nk * NP * NT; e += kF32Threads) {
-            const int t = e % NT, j = (e / NT) % NP, kl = e / (NT * NP);
-            float out[3][5];
-            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, 1.f, sD, out);
-            float* dst = sBc + (size_t)((kl * NT + t) * 5) * KKS + j;
+      // chunks of CHT sub-tets (a runtime value: one copy of the code for every width)
+      const int CHT = first_const ? CHc * NT : CHc;
+      for (int kc = 0; kc < S; kc += CHT) {
+        const int nk = min(CHT, S - kc);
+        // (a) fluxes: items (k, j, t), t fastest; the 15 values of an item go to the columns
+        // (k, t, v) of B^T at rows (d, j)
+        for (int e = tid; e < nk * NP * NTe; e += kF32Threads) {
+          const int et = first_const ? e : e / NT, t = first_const ? 0 : e - et * NT;
+          const int j = et % NP, kl = et / NP;
+          float out[3][5];
+          f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, t, visc, mu, kap, gam, Rg, 1.f, sD, out);
+          float* dst = sBc + (size_t)((kl * NTe + t) * 5) * KKS + j;
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
+          for (int d = 0; d < 3; ++d)
 #pragma unroll
-              for (int v = 0; v < 5; ++v) dst[v * KKS + d * NP] = out[d][v];
-          }
-          __syncthreads();
-          // (b) R[k][t][m][v] = w_t sum_{d,j} S^_d[m][j] B^T[(k, t, v)][d j]: one column per thread,
-          // all Np rows m in registers, S^ as instruction immediates (the zero entries skipped)
-          for (int c = tid; c < nk * NT * 5; c += kF32Threads) {
-            float acc[NP];
+            for (int v = 0; v < 5; ++v) dst[v * KKS + d * NP] = out[d][v];
+        }
+        __syncthreads();
+        // (b) R[k][t][m][v] = w_t dt sum_{d,j} S^_d[m][j] B^T[(k, t, v)][d j]: one column per
+        // thread, all Np rows m in registers, S^ as instruction immediates (zero entries skipped)
+        for (int c = tid; c < nk * NTe * 5; c += kF32Threads) {
+          float acc[NP];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) acc[i] = 0.f;
-            SrefFP32<N>::contract(sBc + (size_t)c * KKS, acc);
-            const int kt = c / 5, v = c - kt * 5;  // kt = kl NT + t
-            const float wt = sW[kt % NT] * dt;  // the time weight and dt, applied once per column
-            float* dst = sR + kt * NP * 5 + v;
+          for (int i = 0; i < NP; ++i) acc[i] = 0.f;
+          SrefFP32<N>::contract(sBc + (size_t)c * KKS, acc);
+          const int kt = c / 5, v = c - kt * 5;  // kt = kl NTe + t
+          const float wt = first_const ? 1.f : sW[kt % NT] * dt;  // time weight and dt, once per column
+          float* dst = sR + kt * NP * 5 + v;
 #pragma unroll
-            for (int i = 0; i < NP; ++i) dst[5 * i] = wt * acc[i];
-          }
-          __syncthreads();
-          // gather this chunk's incidences, in (k, j) order, into the items' registers
+          for (int i = 0; i < NP; ++i) dst[5 * i] = wt * acc[i];
+        }
+        __syncthreads();
+        // gather this chunk's incidences, in (k, j) order, into the items' registers
+#pragma unroll
+        for (int r = 0; r < kF32Items; ++r) {
+          if (inode[r] < 0) continue;
+          const int t = first_const ? 0 : (tid + r * kF32Threads) % NT;
+          gather_in_order(inc, cur[r], cend[r], kc, nk,
+                          [&](int k, int j) { return sR + ((k * NTe + t) * NP + j) * 5; }, racc[r]);
+        }
+        // no barrier here: the next chunk's flux items write only sB, and its contraction,
+        // which overwrites sR, starts after the barrier that follows those items
+      }
+      if constexpr (!TC) {
+        if (first_const) {
+          // r in columns 0..4 (columns 5..7 of the tile are still zero from the cell's start)
 #pragma unroll
           for (int r = 0; r < kF32Items; ++r) {
             if (inode[r] < 0) continue;
-            const int t = (tid + r * kF32Threads) % NT;
-            gather_in_order(inc, cur[r], cend[r], kc, nk,
-                            [&](int k, int j) { return sR + ((k * NT + t) * NP + j) * 5; }, racc[r]);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) srhs[inode[r] * SRN + v] = dt * racc[r][v];
           }
-          // no barrier here: the next chunk's flux items write only sB, and its contraction,
-          // which overwrites sR, starts after the barrier that follows those items
-        }
-      };
-      // First iteration of the mma.sync form: q^0 = u^ at every time node (the initial guess),
-      // so the fluxes at the N+1 time nodes are equal and R_{k,t} = w_t R_k with R_k the
-      // contraction of the time-independent flux; the right-hand side is RHS[n][t] = w_t r[n]
-      // with r[n] = sum_{(k, j) at n} R_k[j], and Y[n][t] = w_t (M_i^-1 r)[n].  One flux per
-      // (sub-tet, node) and one column per (sub-tet, variable) serve all time slices, in
-      // chunks of CHc (N+1) sub-tets (the buffers of the volume term's layout), and the apply
-      // takes the 5 columns of r (one 8-column tile) instead of 5 (N+1).
-      const bool first_const = !TC && it == 1;
-      if (first_const) {
-        float facc[2][5];
-        int fcur[2], fend[2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int n = tid + r * kF32Threads;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) facc[r][v] = 0.f;
-          fcur[r] = n < Ni ? sincp[n] : 0;
-          fend[r] = n < Ni ? sincp[n + 1] : 0;
-        }
-        const int CH1 = CHc * NT;  // sub-tets per chunk: [CH1 5][KKS] fits in sB, [CH1][NP][5] in sR
-        for (int kc = 0; kc < S; kc += CH1) {
-          const int nk = min(CH1, S - kc);
-          for (int e = tid; e < nk * NP; e += kF32Threads) {
-            const int kl = e / NP, j = e % NP;
-            float out[3][5];
-            f32_flux_contract<N>(sq, rec_a(kc + kl), rec_g(kc + kl), j, 0, visc, mu, kap, gam, Rg, 1.f, sD, out);
-            float* dst = sBc + (size_t)(kl * 5) * KKS + j;  // columns (k, v), rows (d, j)
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-#pragma unroll
-              for (int v = 0; v < 5; ++v) dst[v * KKS + d * NP] = out[d][v];
-          }
-          __syncthreads();
-          for (int c = tid; c < nk * 5; c += kF32Threads) {
-            float acc[NP];
-#pragma unroll
-            for (int i = 0; i < NP; ++i) acc[i] = 0.f;
-            SrefFP32<N>::contract(sBc + (size_t)c * KKS, acc);
-            const int kl = c / 5, v = c - kl * 5;
-            float* dst = sR + kl * NP * 5 + v;
-#pragma unroll
-            for (int i = 0; i < NP; ++i) dst[5 * i] = acc[i];
-          }
-          __syncthreads();
-#pragma unroll
-          for (int r = 0; r < 2; ++r)
-            gather_in_order(inc, fcur[r], fend[r], kc, nk, [&](int k, int j) { return sR + (k * NP + j) * 5; },
-                            facc[r]);
-          // no barrier here: the next chunk's flux items write only sB, and its contraction,
-          // which overwrites sR, starts after the barrier that follows those items
-        }
-        // r in columns 0..4 (columns 5..7 of the tile are still zero from the cell's start)
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int n = tid + r * kF32Threads;
-          if (n >= Ni) continue;
-#pragma unroll
-          for (int v = 0; v < 5; ++v) srhs[n * SRN + v] = dt * facc[r][v];
-        }
-      } else if constexpr (NTP == 4) {
-        if (wide) phase1(std::integral_constant<int, 2 * CH>{});
-        else phase1(std::integral_constant<int, CH>{});
-      } else {
-        phase1(std::integral_constant<int, CH>{});
-      }
-      if constexpr (!TC) {
-        if (!first_const) {
+        } else {
 #pragma unroll
           for (int r = 0; r < kF32Items; ++r) {
             if (inode[r] < 0) continue;
@@ -1493,10 +1443,13 @@ __global__ void sub32_kernel(DevMesh m, int64_t T) {
 
 namespace afe {
 
-// FP32 corrector (Sec. 4.4): one block of 128 threads per cell.
+// FP32 corrector (Sec. 4.4): one block of 128 threads per cell, six blocks per SM (the
+// register cap that lets six fit keeps more of M_i^-1 in flight per SM; du waits in shared
+// memory, not registers, until the FP64 correction is known).
 //   r = vol - sum_slots 2 area Z^ G          (fixed-order gather, FP32)
-//   du = M_i^-1 r                            (thread g: 4-row tiles 4g..4g+3, M_i^-1 streamed
-//                                             by 16-byte loads, eight rows in flight)
+//   du = M_i^-1 r                            (thread g: 4-row tiles 4g..4g+3, g + 128, ...;
+//                                             M_i^-1 streamed by 16-byte loads, eight rows in
+//                                             flight)
 //   u += du + (T - w_i . du) / |P_i|         (FP64: T = exact cell total of r, see below)
 // The FP64 correction makes the cell's conserved totals change by exactly
 // T = 1^T r = -sum_slots 2 area sum_b (sum_a Z^[a][b]) G[b] (the volume term sums to zero:
@@ -1504,10 +1457,10 @@ namespace afe {
 constexpr int kCorrThreads = 128;
 
 template <int N>
-__global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __grid_constant__ Batch bt,
+__global__ void __launch_bounds__(kCorrThreads, 6) corrector_f32_kernel(const __grid_constant__ Batch bt,
                                                                         const RefData* __restrict__ ref) {
   constexpr int NF = nf_of(N);
-  extern __shared__ __align__(16) float sr[];  // [Nmax][5]
+  extern __shared__ __align__(16) float sr[];  // [Nmax][5] r, then [Nmax][5] du
   __shared__ float sZ[NF][NF];
   __shared__ double szs[NF];
   __shared__ double sred[2][5][kCorrThreads];
@@ -1563,18 +1516,17 @@ __global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __gri
     for (int v = 0; v < 5; ++v) tot[v] -= twoA * szs[b] * (double)sG[(s * NF + b) * 5 + v];
   }
   __syncthreads();
-  // du = M_i^-1 r, thread g owns rows 4g..4g+3 (and 4(g+128).. for cells over 512 nodes)
+  // du = M_i^-1 r, thread tid owns the column groups g = tid, tid + 128, ... (rows 4g..4g+3)
   const float* minv = m.minv32 + m.minv_ptr[c];
   double wdu[5] = {0, 0, 0, 0, 0};
-  float du[2][4][5];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int g = tid + r * kCorrThreads;
+  float* sdu = sr + (size_t)bt.Nmax * 5;  // du rows, kept in shared memory until corr is known
+  for (int g = tid; 4 * g < Ni; g += kCorrThreads) {
+    float du[1][4][5];  // one column group at a time
+    constexpr int r = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int v = 0; v < 5; ++v) du[r][i][v] = 0.f;
-    if (4 * g >= Ni) continue;
     const float* col = minv + 4 * g;
     for (int l0 = 0; l0 < Ni; l0 += 8) {
       float4 a[8];
@@ -1601,7 +1553,10 @@ __global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __gri
       if (n >= Ni) break;
       const double w = m.wvec[n0 + n];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) wdu[v] += w * (double)du[r][i][v];
+      for (int v = 0; v < 5; ++v) {
+        wdu[v] += w * (double)du[r][i][v];
+        sdu[n * 5 + v] = du[r][i][v];
+      }
     }
   }
   // fixed-order block reductions of T and w . du
@@ -1623,9 +1578,7 @@ __global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __gri
   double corr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) corr[v] = (sred[0][v][0] - sred[1][v][0]) / m.cell_vol[c];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int g = tid + r * kCorrThreads;
+  for (int g = tid; 4 * g < Ni; g += kCorrThreads) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int n = 4 * g + i;
@@ -1634,7 +1587,7 @@ __global__ void __launch_bounds__(kCorrThreads) corrector_f32_kernel(const __gri
       bool bad = false;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        un[v] += (double)du[r][i][v] + corr[v];
+        un[v] += (double)sdu[n * 5 + v] + corr[v];
         bad |= !isfinite(un[v]);
       }
       // rho > 0 and p > 0, with p > 0 tested as rho E > |rho u|^2 / 2 (no division)
