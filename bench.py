@@ -45,7 +45,7 @@ PAPER_CFL = 0.3
 # workload, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 12^3 launch
 # of the current kernel; None until that capture exists.  The fixed-point iterations re-read
 # M_i^-1 from L2, so the traffic grows with the cells, not with the iterations.
-PREDICTOR_N3_DRAM_BYTES_PER_CELL = (813916928 + 41265664) / 1728
+PREDICTOR_N3_DRAM_BYTES_PER_CELL = (812361984 + 40285696) / 1728
 UNIT = "DOF-updates/s"
 
 
