@@ -97,7 +97,10 @@ int main(int argc, char** argv) {
           nz_p += (float)r.S[d][m][j] != 0.0f;
           nz_v += (float)r.S[d][j][m] != 0.0f;
         }
-    std::fprintf(f, "template <>\nstruct SrefFP32<%d> {\n", N);
+    std::fprintf(f, "// node order j = 0 .. Np-1 (barycentric multi-indices alpha_0 alpha_1 alpha_2 alpha_3):");
+    for (int j = 0; j < np; ++j)
+      std::fprintf(f, "%s %d%d%d%d", j % 10 == 0 ? "\n//" : "", r.alpha[j][0], r.alpha[j][1], r.alpha[j][2], r.alpha[j][3]);
+    std::fprintf(f, "\ntemplate <>\nstruct SrefFP32<%d> {\n", N);
     std::fprintf(f, "  static constexpr int KK = %d;   // 3 Np pre-contracted values per column\n", kk_n);
     std::fprintf(f, "  static constexpr int KKS = %d;  // column stride in shared memory (floats)\n",
                  column_stride(kk_n));
