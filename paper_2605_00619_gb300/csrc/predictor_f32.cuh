@@ -260,7 +260,7 @@ constexpr int f32_ntp(int N) { return N == 1 ? 2 : 4; }
 // Row stride of RHS / Y: 24 floats (5 NTP used, the rest zero), a multiple of 8 columns for
 // the tensor-core tiles, and 24 = 8 (mod 16) for conflict-free fragment loads.
 constexpr int f32_rhs_stride(int N) { return (void)N, 24; }
-// Sub-tets per chunk of the right-hand side (16 time-slice pairs of B per chunk).
+// Sub-tets per (narrow) chunk of the right-hand side; wide chunks take twice as many.
 constexpr int f32_chunk(int N) { return f32_ntp(N) == 4 ? 8 : 16; }
 
 // Packed FP32 sub-tet record: adj(J) row-major (9 floats), det J, then the Np cell-local node
