@@ -43,3 +43,25 @@ def test_reference_arm_prints_one_valid_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_predictor_roofline_by_hand():
+    """The roofline fields of the bench line recomputed by hand for the 32^3 N = 3 workload's
+    figures: HBM-bound when the bytes take longer than the 3xTF32 contractions plus the FMA
+    work, the fraction being achieved GB/s over the measured copy bandwidth; tensor-bound
+    (3xTF32 rate = half the BF16 burst over three) otherwise."""
+    peaks = {"hbm_gbs": 6800.3, "bf16_tflops": 1896.7, "sm_max_mhz": 2070.0}
+    f_con, f_pw, abytes, ms = 425031110760.0, 56814155560.0, 14161675240.0, 14.1808256149292
+    r = bench.predictor_roofline(f_con, f_pw, abytes, ms, peaks)
+    t_hbm = abytes / 6800.3e9
+    t_ten = f_con / (1896.7 / 2 / 3 * 1e12)
+    t_fma = f_pw / (152 * 128 * 2 * 2070e6)
+    assert t_hbm > t_ten + t_fma and r["bound"] == "hbm"
+    assert abs(r["frac"] - (abytes / (ms / 1e3) / 1e9) / 6800.3) < 1e-12
+    assert abs(r["frac"] - 0.14685) < 1e-4
+    assert abs(r["roofline_ms"] - 1e3 * t_hbm) < 1e-9 and abs(r["frac_roofline_time"] - r["frac"]) < 1e-12
+    # ten times the contraction work: the tensor pipe sets the roofline
+    r2 = bench.predictor_roofline(10 * f_con, f_pw, abytes, ms, peaks)
+    assert r2["bound"] == "tensor"
+    assert abs(r2["roofline_ms"] - 1e3 * (10 * t_ten + t_fma)) < 1e-9
+    assert abs(r2["frac"] - (10 * f_con / (ms / 1e3) / 1e12) / (1896.7 / 6)) < 1e-12
